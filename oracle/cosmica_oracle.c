@@ -23,13 +23,18 @@
  * is written out in FP64, in the order the step defines, with no fusion:
  * build with -O2 -ffp-contract=off.
  *
+ * Elementary functions (exp, log, sin, cos, tanh, atan) are this file's own
+ * Cody-Waite + series implementations, pinned against libm to a few ulp: the
+ * wavy current sheet makes paths chaotic at the 1-ulp level, so the FP64 GPU
+ * path evaluates the same algorithms to stay bit-identical.
+ *
  * Parity status: Philox is pinned by statistics on the CPU and bit-for-bit
  * against cuRAND's Philox4_32_10 in a GPU test; the isotropic model is pinned
  * by closed forms (mean exit time, exit-point harmonic measure) and by an
  * independent 1-D PDE solver; the full-model coefficients are pinned by
- * symbolic differentiation, finite differences, the closed-form
+ * Cartesian finite differences (Ito drift, curl, divergence), the closed-form
  * gradient-curvature drift and invariants.  Whole-path results of the full
- * model (configs with wavy current sheet) are "parity unpinned" beyond those
+ * model (configs with a wavy current sheet) are "parity unpinned" beyond those
  * piecewise pins: no independent solution exists.
  */
 #include <math.h>
@@ -95,6 +100,181 @@ typedef struct {
     double m0;            /* rest mass per nucleon, GeV */
 } orc_species;
 
+
+/* ======================================================================= */
+/* Deterministic FP64 elementary functions.                                 */
+/* The wavy current sheet makes paths sensitive to single-ulp differences, */
+/* so the oracle and the FP64 GPU path evaluate every transcendental with  */
+/* the same classical algorithm in plain IEEE +,-,*,/ (no fused operations):*/
+/* Cody-Waite argument reduction (Cody & Waite, "Software Manual for the   */
+/* Elementary Functions", 1980) followed by truncated Taylor series.        */
+/* Accuracy (pinned against libm in the tests): a few ulp; tanh to 4e-16   */
+/* absolute.  sqrt is IEEE correctly rounded on both sides and stays libm. */
+/* ======================================================================= */
+static double dm_from_bits(uint64_t b) { double x; memcpy(&x, &b, 8); return x; }
+static uint64_t dm_bits(double x) { uint64_t b; memcpy(&b, &x, 8); return b; }
+
+/* ln 2 split so that k * DM_LN2_HI is exact for |k| < 2^21 */
+#define DM_LN2_HI   0.6931471803691238
+#define DM_LN2_LO   1.9082149292705877e-10
+#define DM_LOG2E    1.4426950408889634
+/* pi/2 split in three 33-bit pieces */
+#define DM_PIO2_1   1.5707963267341256
+#define DM_PIO2_2   6.077100506303966e-11
+#define DM_PIO2_3   2.0222662487959506e-21
+#define DM_2_OVER_PI 0.6366197723675814
+#define DM_PI_2     1.5707963267948966
+#define DM_PI_4     0.7853981633974483
+#define DM_PI_8     0.39269908169872414
+#define DM_TAN_PI_8 0.41421356237309503
+#define DM_SQRT2    1.4142135623730951
+
+double orc_exp(double x)
+{
+    if (!(x < 709.0)) return (x != x) ? x : 1.0 / 0.0;
+    if (x < -708.0) return 0.0;
+    double k = floor(x * DM_LOG2E + 0.5);
+    double r = (x - k * DM_LN2_HI) - k * DM_LN2_LO;        /* |r| <= ln2 / 2 */
+    double p = 1.0 / 6227020800.0;                          /* 1/13! */
+    p = p * r + 1.0 / 479001600.0;
+    p = p * r + 1.0 / 39916800.0;
+    p = p * r + 1.0 / 3628800.0;
+    p = p * r + 1.0 / 362880.0;
+    p = p * r + 1.0 / 40320.0;
+    p = p * r + 1.0 / 5040.0;
+    p = p * r + 1.0 / 720.0;
+    p = p * r + 1.0 / 120.0;
+    p = p * r + 1.0 / 24.0;
+    p = p * r + 1.0 / 6.0;
+    p = p * r + 0.5;
+    p = p * r + 1.0;
+    p = p * r + 1.0;
+    int ki = (int)k;
+    return p * dm_from_bits((uint64_t)(ki + 1023) << 52);
+}
+
+double orc_log(double x)
+{
+    if (!(x > 0.0)) return (x == 0.0) ? -1.0 / 0.0 : 0.0 / 0.0;
+    if (x == 1.0 / 0.0) return x;
+    uint64_t b = dm_bits(x);
+    int e = (int)((b >> 52) & 0x7ff) - 1023;
+    double m = dm_from_bits((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull);  /* [1, 2) */
+    if (m > DM_SQRT2) { m = m * 0.5; e = e + 1; }
+    double s = (m - 1.0) / (m + 1.0);                       /* |s| <= 0.1716 */
+    double s2 = s * s;
+    /* log m = 2 atanh s = 2 s (1 + s^2/3 + s^4/5 + ... + s^22/23) */
+    double q = 1.0 / 23.0;
+    q = q * s2 + 1.0 / 21.0;
+    q = q * s2 + 1.0 / 19.0;
+    q = q * s2 + 1.0 / 17.0;
+    q = q * s2 + 1.0 / 15.0;
+    q = q * s2 + 1.0 / 13.0;
+    q = q * s2 + 1.0 / 11.0;
+    q = q * s2 + 1.0 / 9.0;
+    q = q * s2 + 1.0 / 7.0;
+    q = q * s2 + 1.0 / 5.0;
+    q = q * s2 + 1.0 / 3.0;
+    q = q * s2 + 1.0;
+    double lm = 2.0 * s * q;
+    double de = (double)e;
+    return de * DM_LN2_HI + (de * DM_LN2_LO + lm);
+}
+
+void orc_sincos(double x, double *sn, double *cs)
+{
+    double k = floor(x * DM_2_OVER_PI + 0.5);
+    double r = ((x - k * DM_PIO2_1) - k * DM_PIO2_2) - k * DM_PIO2_3;   /* |r| <= pi/4 */
+    double r2 = r * r;
+    double ps = -1.0 / 121645100408832000.0;                /* -1/19! */
+    ps = ps * r2 + 1.0 / 355687428096000.0;
+    ps = ps * r2 - 1.0 / 1307674368000.0;
+    ps = ps * r2 + 1.0 / 6227020800.0;
+    ps = ps * r2 - 1.0 / 39916800.0;
+    ps = ps * r2 + 1.0 / 362880.0;
+    ps = ps * r2 - 1.0 / 5040.0;
+    ps = ps * r2 + 1.0 / 120.0;
+    ps = ps * r2 - 1.0 / 6.0;
+    ps = ps * r2 + 1.0;
+    double sr = r * ps;
+    double pc = 1.0 / 2432902008176640000.0;                /* 1/20! */
+    pc = pc * r2 - 1.0 / 6402373705728000.0;
+    pc = pc * r2 + 1.0 / 20922789888000.0;
+    pc = pc * r2 - 1.0 / 87178291200.0;
+    pc = pc * r2 + 1.0 / 479001600.0;
+    pc = pc * r2 - 1.0 / 3628800.0;
+    pc = pc * r2 + 1.0 / 40320.0;
+    pc = pc * r2 - 1.0 / 720.0;
+    pc = pc * r2 + 1.0 / 24.0;
+    pc = pc * r2 - 0.5;
+    pc = pc * r2 + 1.0;
+    double cr = pc;
+    int q = (int)((long long)k & 3);
+    if (q == 0)      { *sn = sr;  *cs = cr;  }
+    else if (q == 1) { *sn = cr;  *cs = -sr; }
+    else if (q == 2) { *sn = -sr; *cs = -cr; }
+    else             { *sn = -cr; *cs = sr;  }
+}
+
+double orc_tanh(double x)
+{
+    double a = fabs(x);
+    double t;
+    if (a > 20.0) t = 1.0;
+    else {
+        double e = orc_exp(2.0 * a);
+        t = 1.0 - 2.0 / (e + 1.0);
+    }
+    return (x < 0.0) ? -t : t;
+}
+
+double orc_atan(double x)
+{
+    double a = fabs(x);
+    int inv = 0;
+    if (a > 1.0) { a = 1.0 / a; inv = 1; }
+    double base = 0.0, y = a;
+    if (a > 0.66817863791929891) {              /* tan(3 pi / 16) */
+        y = (a - 1.0) / (a + 1.0);
+        base = DM_PI_4;
+    } else if (a > 0.19891236737965800) {       /* tan(pi / 16) */
+        y = (a - DM_TAN_PI_8) / (1.0 + a * DM_TAN_PI_8);
+        base = DM_PI_8;
+    }
+    double y2 = y * y;                          /* |y| <= 0.2 */
+    double q = -1.0 / 23.0;
+    q = q * y2 + 1.0 / 21.0;
+    q = q * y2 - 1.0 / 19.0;
+    q = q * y2 + 1.0 / 17.0;
+    q = q * y2 - 1.0 / 15.0;
+    q = q * y2 + 1.0 / 13.0;
+    q = q * y2 - 1.0 / 11.0;
+    q = q * y2 + 1.0 / 9.0;
+    q = q * y2 - 1.0 / 7.0;
+    q = q * y2 + 1.0 / 5.0;
+    q = q * y2 - 1.0 / 3.0;
+    q = q * y2 + 1.0;
+    double res = base + y * q;
+    if (inv) res = DM_PI_2 - res;
+    return (x < 0.0) ? -res : res;
+}
+
+/* Element-wise evaluation for the tests: 0 exp, 1 log, 2 sin, 3 cos, 4 tanh, 5 atan. */
+void orc_fn(int which, uint64_t n, const double *x, double *y)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        double s, c;
+        switch (which) {
+        case 0: y[i] = orc_exp(x[i]); break;
+        case 1: y[i] = orc_log(x[i]); break;
+        case 2: orc_sincos(x[i], &s, &c); y[i] = s; break;
+        case 3: orc_sincos(x[i], &s, &c); y[i] = c; break;
+        case 4: y[i] = orc_tanh(x[i]); break;
+        default: y[i] = orc_atan(x[i]); break;
+        }
+    }
+}
+
 /* ======================================================================= */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).                       */
 /* Round: two 32x32->64 products of the even words with the multipliers    */
@@ -142,13 +322,16 @@ void orc_normals(uint64_t seed, uint64_t pid, uint32_t step, uint32_t tag, doubl
     double u1 = ((double)w[1] + 0.5) * two_m32;
     double u2 = ((double)w[2] + 0.5) * two_m32;
     double u3 = ((double)w[3] + 0.5) * two_m32;
-    double rho0 = sqrt(-2.0 * log(u0));
-    double rho2 = sqrt(-2.0 * log(u2));
+    double rho0 = sqrt(-2.0 * orc_log(u0));
+    double rho2 = sqrt(-2.0 * orc_log(u2));
     double a1 = ORC_TWO_PI * u1;
     double a3 = ORC_TWO_PI * u3;
-    z[0] = rho0 * cos(a1);
-    z[1] = rho0 * sin(a1);
-    z[2] = rho2 * cos(a3);
+    double s1, c1, s3, c3;
+    orc_sincos(a1, &s1, &c1);
+    orc_sincos(a3, &s3, &c3);
+    z[0] = rho0 * c1;
+    z[1] = rho0 * s1;
+    z[2] = rho2 * c3;
 }
 
 void orc_normals_many(uint64_t seed, uint64_t pid0, uint64_t n, uint32_t step, double *z)
@@ -195,7 +378,7 @@ static void wind(const orc_params *p, double th, double *V, double *dV)
     double lat = 0.5 * ORC_PI - th;
     double lat_f = p->lat_fast_deg * ORC_DEG;
     double dlat = p->dlat_deg * ORC_DEG;
-    double t = tanh((fabs(lat) - lat_f) / dlat);
+    double t = orc_tanh((fabs(lat) - lat_f) / dlat);
     *V = Vs + (Vf - Vs) * 0.5 * (1.0 + t);
     /* d|lat|/dth = -sgn(lat) */
     *dV = (Vf - Vs) * 0.5 * (1.0 - t * t) / dlat * (-sgn(lat));
@@ -216,11 +399,12 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
                       double r, double th, double ph, double lnP, orc_coef *c)
 {
     memset(c, 0, sizeof(*c));
-    double sin_th = sin(th), cos_th = cos(th);
+    double sin_th, cos_th;
+    orc_sincos(th, &sin_th, &cos_th);
     double cot_th = cos_th / sin_th;
 
     /* rigidity and speed: P = (A/|Z|) p_n, beta = p_n / sqrt(p_n^2 + m0^2) */
-    c->P = exp(lnP);
+    c->P = orc_exp(lnP);
     double aoz = sp->A / fabs(sp->Z);
     double pn = c->P / aoz;
     c->beta = pn / sqrt(pn * pn + sp->m0 * sp->m0);
@@ -230,7 +414,7 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
 
     /* termination shock: g(r) = 1 - (1 - f)(1 + tanh((r - Rts)/d))/2 */
     if (p->R_ts > 0.0) {
-        double t = tanh((r - p->R_ts) / p->dts_AU);
+        double t = orc_tanh((r - p->R_ts) / p->dts_AU);
         c->g = 1.0 - (1.0 - p->ts_K_factor) * 0.5 * (1.0 + t);
         c->dg_dr = -(1.0 - p->ts_K_factor) * 0.5 * (1.0 - t * t) / p->dts_AU;
     } else {
@@ -332,12 +516,15 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
     c->delta_cs = 0.0;
     if (p->isotropic == 0.0 && p->hcs_on != 0.0) {
         double Omega = ORC_TWO_PI / p->rot_period_day;
-        double ta = tan(p->tilt_deg * ORC_DEG);
+        double sa, ca;
+        orc_sincos(p->tilt_deg * ORC_DEG, &sa, &ca);
+        double ta = sa / ca;
         double phs = ph + Omega * r / c->V;
         double dphs_dr = Omega / c->V;
         double dphs_dth = -Omega * r * c->dV_dth / (c->V * c->V);
-        double sp_ = sin(phs), cp_ = cos(phs);
-        double th_cs = 0.5 * ORC_PI + atan(ta * sp_);
+        double sp_, cp_;
+        orc_sincos(phs, &sp_, &cp_);
+        double th_cs = 0.5 * ORC_PI + orc_atan(ta * sp_);
         double dthcs = ta * cp_ / (1.0 + ta * ta * sp_ * sp_);   /* d th_cs / d phs */
         /* half-width: max(2 r_L / r, delta_min), r_L = P/(c |B|) */
         double D = c->P * 1e9 / (ORC_C_MS * B0 * 1e-9 * ORC_AU_M);
@@ -354,7 +541,7 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
             delta = dmin;
         }
         double u = (th_cs - th) / delta;
-        double h = tanh(u);
+        double h = orc_tanh(u);
         double du_dr = (dthcs * dphs_dr - u * dd_dr) / delta;
         double du_dth = (dthcs * dphs_dth - 1.0 - u * dd_dth) / delta;
         double du_dph = dthcs / delta;
@@ -481,7 +668,8 @@ static void em_step(const orc_params *p, const orc_species *sp, uint64_t seed, u
     eval_coef(p, sp, x->r, x->th, x->ph, x->lnP, &c);
     double dt = c.dt;
     double sdt = sqrt(dt);
-    double sin_th = sin(x->th);
+    double sin_th, cos_th;
+    orc_sincos(x->th, &sin_th, &cos_th);
     double Lz_r = c.L[0][0] * z[0];
     double Lz_th = c.L[1][0] * z[0] + c.L[1][1] * z[1];
     double Lz_ph = c.L[2][0] * z[0] + c.L[2][1] * z[1] + c.L[2][2] * z[2];
@@ -527,7 +715,7 @@ static double rigidity(const orc_species *sp, double T)
 static void init_state(const orc_params *p, const orc_species *sp, double T_in, orc_state *x)
 {
     x->r = p->r0; x->th = p->th0; x->ph = p->ph0;
-    x->lnP = log(rigidity(sp, T_in));
+    x->lnP = orc_log(rigidity(sp, T_in));
     x->s = 0.0; x->k = 0u; x->status = ORC_RUNNING;
 }
 

@@ -96,6 +96,7 @@ def lib():
                                     C.c_uint64, C.c_uint64, C.c_uint32, f64p]
             L.orc_trace.restype = C.c_int
             L.orc_max_threads.restype = C.c_int
+            L.orc_fn.argtypes = [C.c_int, C.c_uint64, f64p, f64p]
             assert L.orc_eval_n() == len(EVAL_NAMES)
             _lib = L
     return _lib
@@ -194,6 +195,17 @@ def trace(p: dict, species: dict, T_in: float, pid: int, seed: int, nsteps: int)
     out = np.zeros((nsteps, 6), np.float64)
     m = lib().orc_trace(C.byref(_params(p)), C.byref(_species(species)), T_in, pid, seed, nsteps, out)
     return out[:m]
+
+
+FN_CODES = {"exp": 0, "log": 1, "sin": 2, "cos": 3, "tanh": 4, "atan": 5}
+
+
+def fn(name: str, x) -> np.ndarray:
+    """The oracle's deterministic FP64 elementary function `name` applied element-wise."""
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.empty_like(x)
+    lib().orc_fn(FN_CODES[name], x.size, x, y)
+    return y
 
 
 def max_threads() -> int:
