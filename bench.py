@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark of the COSMICA hot path on GB300: SDE steps/s and spectra/s.
+
+One bench "step" = one pass of the whole hot path over one batch of synthetic
+input: work expansion into the device queue, the persistent propagation
+launch (RNG, coefficients, Euler-Maruyama until every path exits), the
+warp-aggregated histogram and the spectrum kernel.
+
+Default workload (--workload c2): the full heliospheric model (Parker field,
+two-speed wind, drifts, wavy current sheet, tilt 20 deg, qA > 0) for protons
+at 30 log-spaced energies in 0.1-100 GeV with 20 000 quasi-particles each,
+mixed precision (FP32 coefficients and normals, compensated FP32
+accumulation, exact boundary test), batched persistent launch.  The plain
+FP64 GPU path is timed on the same workload and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run; each rank propagates its own
+copy of the workload with disjoint particle identities (weak scaling, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2502_06319_gb300 import workloads as W  # noqa: E402
+
+METRIC = "SDE steps/s & spectra/s, FP32-batched vs plain FP64 GPU at <=0.5% spectrum error"
+
+# Algorithmic work of one mixed-precision step, tallied from the source of
+# the step (model32.cuh + the loop of k_mixed.cu): FP32 add/mul/fma, SFU
+# (MUFU) operations and integer operations of Philox, each one issue slot.
+# See DESIGN.md "Roofline" for the tally.
+ALG_INST_PER_STEP = {"fp32": 196, "mufu": 21, "int": 78, "fp32_ff_acc": 50}
+ALG_INST_TOTAL = sum(ALG_INST_PER_STEP.values())
+SM_LANES_PER_CLK = 128      # 4 SMSPs x 32 lanes: one warp instruction per SMSP per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--c3-scale", type=float, default=1.0, help="scale of config-3 particle counts")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_f64acc", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="particles per energy in the oracle sample")
+    return ap.parse_args()
+
+
+def workload(args):
+    """Jobs (one per spectrum) of the chosen configuration."""
+    if args.workload == "c1":
+        return [W.config1()], "config1: full model FP64-spec, proton, 10 energies x 5000"
+    if args.workload == "c2":
+        return [W.config2()], "config2: full model, proton, 30 energies x 20000"
+    jobs = W.config3(scale=args.c3_scale)
+    return jobs, f"config3: 64 heliospheres x 3 species x 30 energies, counts 1e3-5e4 (scale {args.c3_scale})"
+
+
+def items_of(jobs, rank):
+    """Work items (param_idx, species_idx, T, n, first_pid, seed) of all jobs; a rank's copy
+    uses disjoint particle identities and its own seeds."""
+    params, pkeys, species, skeys, items = [], {}, [], {}, []
+    pid = 0
+    base = rank * (1 << 40)
+    for j in jobs:
+        pk = tuple(sorted(j.params.items()))
+        if pk not in pkeys:
+            pkeys[pk] = len(params)
+            params.append(j.params)
+        sk = tuple(sorted(j.species.items()))
+        if sk not in skeys:
+            skeys[sk] = len(species)
+            species.append(j.species)
+        for T, n in zip(j.T_in, j.n_per_energy):
+            items.append((pkeys[pk], skeys[sk], T, n, base + pid, j.seed + 7919 * rank))
+            pid += n
+    return params, species, items
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = [ln.split(",") for ln in open(self.f.name).read().strip().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1])); mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(jobs, sample_per_energy: int):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    from oracle import oracle as O
+    O.build()
+    threads = O.max_threads()
+    job = jobs[0]
+    sel = []
+    off = 0
+    for n in job.n_per_energy:
+        sel.extend(range(off, off + min(n, sample_per_energy)))
+        off += n
+    t0 = time.perf_counter()
+    out = O.job_run(job, select=np.asarray(sel), threads=threads)
+    dt = time.perf_counter() - t0
+    steps = int(out["steps"].astype(np.int64).sum())
+    return {"value": steps / dt, "unit": "steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(sel)} quasi-particles ({sample_per_energy} per energy of {job.name}), "
+                      f"{steps} steps in {dt:.1f} s", "seconds": dt, "steps": steps}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on this machine's host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    jobs, desc = workload(args)
+    sample = args.cpu_sample or (40 if args.workload != "c1" else 100)
+    if args.warmup > 0:
+        cpu_baseline(jobs, max(2, sample // 10))
+    vals, secs, steps = [], 0.0, 0
+    for _ in range(max(1, args.steps)):
+        cb = cpu_baseline(jobs, sample)
+        vals.append(cb["value"]); secs += cb["seconds"]; steps += cb["steps"]
+    v = steps / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "sample_per_energy": sample},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2502_06319_gb300 import cosmica as cz
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU: the hot path has no CPU implementation")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    jobs, desc = workload(args)
+    prec = {"mixed": cz.PREC_MIXED, "mixed_f64acc": cz.PREC_MIXED_F64ACC, "fp64": cz.PREC_FP64}[args.precision]
+    params, species, items = items_of(jobs, rank)
+    n_total = sum(i[3] for i in items)
+    n_spectra = len(jobs)
+    nb = jobs[0].bins.n
+    bins = cz.make_bins(jobs[0].bins.P_min, jobs[0].bins.P_max, nb)
+    stream = torch.cuda.Stream()
+
+    def make_batch(precision):
+        return cz.cosmica_batch_create([cz.make_params(p, precision) for p in params],
+                                       [cz.make_species(s) for s in species])
+
+    arr = cz.make_items(items)
+    nI = len(items)
+    batch = make_batch(prec)
+    tune, tune_rate = cz.cosmica_autotune(batch, arr, nI)
+    tune.use_graph = 1
+    out = cz.ExitBuffers(n_total)
+    J = torch.empty(nI, dtype=torch.float64, device="cuda")
+    S = torch.empty_like(J)
+    H = torch.empty(nI * (nb + 3), dtype=torch.int64, device="cuda")
+    steps_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
+
+    def one_pass(b, t):
+        cz.cosmica_batch_run(b, arr, nI, out, tuning=t, steps_out=steps_dev, stream=stream)
+        cz.cosmica_batch_spectrum(b, arr, nI, out, bins, J, S, H, stream=stream)
+
+    def timed(b, t, warm, k):
+        with torch.cuda.stream(stream):
+            for _ in range(warm):
+                one_pass(b, t)
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms, steps, launches = [], 0, cz.cosmica_launch_count()
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                one_pass(b, t)
+                e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            steps += int(steps_dev.item())
+        launches = cz.cosmica_launch_count() - launches
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        return ms, steps, launches
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms, steps_done, launches = timed(batch, tune, args.warmup, args.steps)
+    clk = clocks.stop()
+    tot_ms = sum(ms)
+    if dist:
+        tt = torch.tensor([tot_ms, float(steps_done)], dtype=torch.float64, device="cuda")
+        mx = tt.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        tot_ms, steps_all = float(mx[0]), float(sm[1])
+    else:
+        steps_all = float(steps_done)
+    steps_per_s = steps_all / (tot_ms * 1e-3)
+    spectra_per_s = n_spectra * world * args.steps / (tot_ms * 1e-3)
+    Jm = J.cpu().numpy().copy()
+
+    # end to end through the public API, timed on the host: each step the library copies the
+    # step's inputs (work items, prefix sums) host -> device inside cosmica_batch_run, and the
+    # spectrum and histogram are read back into pinned host memory
+    J_h = torch.empty(nI, dtype=torch.float64, pin_memory=True)
+    S_h = torch.empty(nI, dtype=torch.float64, pin_memory=True)
+    H_h = torch.empty(nI * (nb + 3), dtype=torch.int64, pin_memory=True)
+    e2e_steps, e2e_s = 0, 0.0
+    for it in range(1 + max(1, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            one_pass(batch, tune)
+            J_h.copy_(J, non_blocking=True)
+            S_h.copy_(S, non_blocking=True)
+            H_h.copy_(H, non_blocking=True)
+        stream.synchronize()
+        dt = time.perf_counter() - t0
+        if it > 0:
+            e2e_s += dt
+            e2e_steps += int(steps_dev.item())
+    h2d = nI * 32 + (nI + 1) * 8
+    d2h = 2 * nI * 8 + nI * (nb + 3) * 8
+
+    # plain FP64 GPU path on the same workload (one-thread-per-particle launch)
+    fp64 = None
+    if not args.no_fp64 and prec != cz.PREC_FP64:
+        b64 = make_batch(cz.PREC_FP64)
+        ms64, st64, _ = timed(b64, None, 1, 1)
+        J64 = J.cpu().numpy().copy()
+        fp64 = {"steps_per_s": st64 / (sum(ms64) * 1e-3), "ms_per_step": sum(ms64),
+                "max_spectrum_rel_diff_mixed_vs_fp64": float(np.nanmax(np.abs(Jm / J64 - 1)))}
+        cz.cosmica_batch_destroy(b64)
+
+    # roofline: algorithmic issue slots per step x steps/s against the SM issue rate
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    f_mhz = clk.get("sm_mhz") or 2070.0
+    peak = SM_LANES_PER_CLK * sm_count * f_mhz * 1e6 / 1e12          # T inst/s
+    achieved = ALG_INST_TOTAL * steps_per_s / world / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
+            "traffic": None, "peak_basis": f"{SM_LANES_PER_CLK} lanes/clk/SM x {sm_count} SMs x "
+                                           f"{f_mhz:.0f} MHz (median SM clock sampled under load)",
+            "alg_inst_per_step": ALG_INST_PER_STEP}
+
+    line = {"metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff" if prec == cz.PREC_MIXED else
+            ("f32+f64acc" if prec == cz.PREC_MIXED_F64ACC else "f64"), "data": "synthetic",
+            "config": {"workload": desc, "particles_per_gpu": n_total, "spectra_per_step": n_spectra,
+                       "precision": args.precision, "tuning": {"block": tune.block,
+                                                               "blocks_per_sm": tune.blocks_per_sm,
+                                                               "graph": bool(tune.use_graph)},
+                       "l2": "flushed (256 MB write) before every timed step", "parallelism": f"weak x{world}"},
+            "spectra_per_s": spectra_per_s,
+            "e2e": {"value": e2e_steps / e2e_s if e2e_s else None, "unit": "steps/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clk, "roofline": roof, "fp64_plain": fp64}
+    if rank == 0 and not args.no_cpu and world == 1:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(jobs, args.cpu_sample or 40).items()
+                                if k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    cz.cosmica_batch_destroy(batch)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,281 @@
+/*
+ * cosmica.h -- C ABI of libcosmica, a GB300 (sm_103a) implementation of the
+ * hot path of COSMICA (Cavallotto, Della Torre, La Vacca, Gervasi,
+ * arXiv 2502.06319): backward-in-time Euler-Maruyama integration of the
+ * Parker-transport SDEs in momentum form, one GPU thread per quasi-particle,
+ * followed by binning of the exit rigidities and the LIS-weighted spectrum.
+ *
+ * Conventions shared by every entry point
+ *   - Ownership: the caller owns every input and output buffer.  The library
+ *     owns only the opaque handles it returns (model, batch, server) and the
+ *     device scratch inside them.
+ *   - Memory: arguments documented "device" must be device pointers of the
+ *     current CUDA device; "host" arguments are ordinary host memory.  The
+ *     exit-state buffers of cosmica_propagate / cosmica_batch_run may be host
+ *     memory too (pinned or pageable): the library then stages through its
+ *     own device scratch and copies the result back on the stream.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     Calls are stream-ordered and do not synchronise the host, except
+ *     where a host output is requested (then they synchronise the stream).
+ *   - Errors: every call returns a cosmica_status; on failure a thread-local
+ *     message is available from cosmica_last_error().  No call aborts, traps
+ *     or spins without bound: the only loops on the device are the particle
+ *     step loops, each bounded by cosmica_params.max_steps.
+ *   - Particle identity: quasi-particle i of a work item has pid =
+ *     first_pid + i.  Its Philox stream is keyed by (seed, pid, step) only, so
+ *     results do not depend on batching, ordering or launch shape.
+ */
+#ifndef COSMICA_H
+#define COSMICA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define COSMICA_ABI_VERSION 1u
+
+typedef enum {
+    COSMICA_OK = 0,
+    COSMICA_ERR_INVALID = 1,   /* bad argument; nothing was launched            */
+    COSMICA_ERR_OOM = 2,       /* a device or pinned allocation failed          */
+    COSMICA_ERR_CUDA = 3,      /* a CUDA runtime call or launch failed          */
+    COSMICA_ERR_TIMEOUT = 4,   /* a bounded host wait ran out                   */
+    COSMICA_ERR_BUSY = 5       /* result not ready yet (server poll)            */
+} cosmica_status;
+
+/* Arithmetic of the step. */
+enum {
+    COSMICA_PREC_FP64 = 0,        /* FP64 everywhere; built without FMA contraction
+                                     and with deterministic elementary functions  */
+    COSMICA_PREC_MIXED = 1,       /* FP32 coefficients, tensor root and normals;
+                                     compensated FP32 (float-float) accumulation of
+                                     r, theta, phi, lnP, s; exact boundary test  */
+    COSMICA_PREC_MIXED_F64ACC = 2 /* FP32 coefficients; FP64 accumulation and test */
+};
+
+/* Per-path status in cosmica_exit_states.status. */
+enum {
+    COSMICA_PATH_RUNNING = 0,
+    COSMICA_PATH_EXIT = 1,        /* crossed the outer boundary r >= R_out      */
+    COSMICA_PATH_STEP_LIMIT = 2,  /* reached max_steps                          */
+    COSMICA_PATH_NONFINITE = 3    /* the state became NaN / Inf                 */
+};
+
+/*
+ * Heliospheric model and integration parameters (Sec. II.B: inner heliosphere
+ * with a Parker-spiral field and latitude-dependent wind; the termination
+ * shock separates the heliosheath).  The paper defers the SDE coefficients to
+ * another publication; the library implements this reading:
+ *   wind    V(th) = Vs + (Vf-Vs) (1 + tanh((|lat| - lat_fast)/dlat)) / 2, radial
+ *   field   B = A h B0 (1 AU/r)^2 (e_r - Gamma e_ph), Gamma = Omega r sin(th)/V,
+ *           B0 chosen so that |B|(1 AU, equator) = B1AU_nT
+ *   K       K_par = K0 beta P[GV] g(r) along b, K_perp,r = kperp_r_frac K_par,
+ *           K_perp,th = kperp_th_frac K_par; g = 1 - (1-ts_K_factor)(1+tanh((r-R_ts)/dts))/2
+ *   drift   v_d = sgn(q A) curl(kappa_A h e_B), kappa_A = beta P / (3 |B|),
+ *           h = tanh((th_cs - th)/delta), th_cs = pi/2 + atan(tan(tilt) sin(ph + Omega r/V)),
+ *           delta = max(2 r_L / r, dcs_min)
+ *   SDE     (Eq. 3, Eq. 5, Eq. 6) dx = (div K - V - v_d) ds + sqrt(2K) dW,
+ *           d lnP = 2V/(3r) ds, Euler-Maruyama, backward time s [day]
+ *   dt      dt_fixed if > 0, else min(dt_max, eps_adv 2K_rr/A_r^2, eps_diff r^2/K_rr,
+ *           eps_diff (r delta)^2/K_th) floored at dt_min (the advective step
+ *           is kept small against the diffusive one, Sec. IV.A)
+ *   bounds  absorbing at r >= R_out, reflecting at r_in, theta folded at the poles
+ * isotropic != 0 selects the spherically symmetric "1D model" of Sec. IV.B:
+ *   K = K0 beta P times the identity, uniform wind V_const_kms, no drift.
+ * Fill with cosmica_params_default() and override; struct_size and version
+ * guard the ABI.
+ */
+typedef struct {
+    uint32_t struct_size;      /* = sizeof(cosmica_params)                 */
+    uint32_t version;          /* = COSMICA_ABI_VERSION                    */
+    double K0;                 /* AU^2/day                                 */
+    double kperp_r_frac;
+    double kperp_th_frac;
+    double B1AU_nT;
+    double V_slow_kms;
+    double V_fast_kms;
+    double lat_fast_deg;
+    double tilt_deg;
+    int32_t polarity;          /* +1 or -1: sign of A                      */
+    int32_t drift_on;          /* 0/1                                      */
+    int32_t hcs_on;            /* 0/1: wavy sheet; 0 = unipolar (h = +1)   */
+    int32_t isotropic;         /* 0/1                                      */
+    double R_out_AU;
+    double R_ts_AU;            /* 0 = no termination shock                 */
+    double ts_K_factor;
+    double r_in_AU;
+    double dt_max_day;
+    double dt_fixed_day;       /* > 0: fixed step                          */
+    double dt_min_day;
+    double eps_adv;
+    double eps_diff;
+    double V_const_kms;        /* wind of the isotropic model              */
+    double dlat_deg;
+    double dts_AU;
+    double dcs_min_deg;
+    double rot_period_day;
+    double r0_AU, th0_rad, ph0_rad;   /* detection point (start of the backward paths) */
+    uint32_t max_steps;        /* step limit per path (>= 1)               */
+    int32_t precision;         /* COSMICA_PREC_*                           */
+} cosmica_params;
+
+/* Particle species: mass number A, signed charge number Z, rest mass per
+ * nucleon m0 [GeV].  Rigidity P = (A/|Z|) sqrt(T (T + 2 m0)) for kinetic
+ * energy per nucleon T [GeV/n]. */
+typedef struct {
+    int32_t A;
+    int32_t Z;
+    double m0_GeV;
+} cosmica_species;
+
+/* Exit states, one entry per quasi-particle, structure of arrays.  Entry g is
+ * the g-th particle in work-item order (item 0's particles first).  Written
+ * once per particle; caller-owned, device or host memory (all arrays in the
+ * same space), each of length n. */
+typedef struct {
+    double *r, *th, *ph, *lnP, *s;   /* post-step state at exit [AU, rad, rad, ln GV, day] */
+    uint32_t *steps;                 /* Euler-Maruyama steps taken               */
+    uint8_t *status;                 /* COSMICA_PATH_*                           */
+    uint32_t *item;                  /* work item (energy index for propagate)   */
+    uint64_t n;
+} cosmica_exit_states;
+
+/* Local interstellar spectrum per GeV/n (Sec. II.B, Eq. 4).
+ * kind 0: analytic J = T^-2.7 / (1 + T^-3.7); kind 1: log-log table of n host
+ * points (ln T ascending, ln J), linear in between, clamped at the ends. */
+typedef struct {
+    int32_t kind;
+    uint32_t n;
+    const double *lnT;
+    const double *lnJ;
+} cosmica_lis;
+
+/* Exit-rigidity histogram: nbins log-spaced bins on [P_min, P_max] GV. */
+typedef struct {
+    double P_min_GV;
+    double P_max_GV;
+    uint32_t nbins;
+} cosmica_bins;
+
+/* Histogram layout per work item, (nbins + 3) uint64 counters:
+ * [0] underflow, [1 .. nbins] bins, [nbins + 1] overflow, [nbins + 2] failed
+ * (step limit or non-finite). */
+#define COSMICA_HIST_STRIDE(nbins) ((nbins) + 3u)
+
+typedef struct cosmica_model cosmica_model;
+
+/* Fill *p with the library defaults (the full model of the reading above,
+ * 100 AU, adaptive dt, FP64). */
+void cosmica_params_default(cosmica_params *p);
+
+/* Create a model from one parameter set (host).  Validates the parameters,
+ * uploads them and derives the per-set constants on the device (synchronous).
+ * *out receives the handle; destroy it with cosmica_model_destroy. */
+cosmica_status cosmica_model_create(const cosmica_params *params, cosmica_model **out);
+void cosmica_model_destroy(cosmica_model *model);
+
+/*
+ * Propagate quasi-particles backward in time until they leave the heliosphere
+ * (Sec. IV.A: one thread per quasi-particle, a propagation kernel evolving
+ * each path until a boundary is reached).
+ *   species        host, one species for all energies
+ *   T_in_GeVn      host [n_energies], kinetic energy per nucleon at the start
+ *   n_per_energy   host [n_energies], quasi-particles per energy (0 allowed)
+ *   seed           Philox key
+ *   out            exit states; out->n must equal sum(n_per_energy); out->item
+ *                  receives the energy index
+ * Particle g has pid = g.  The FP64 path launches one thread per particle;
+ * the mixed paths run the persistent work-queue kernel.
+ * Errors: INVALID (sizes, null pointers), OOM, CUDA. */
+cosmica_status cosmica_propagate(cosmica_model *model, const cosmica_species *species,
+                                 const double *T_in_GeVn, uint32_t n_energies,
+                                 const uint32_t *n_per_energy, uint64_t seed,
+                                 cosmica_exit_states *out, void *stream);
+
+/*
+ * Bin the exit rigidities and form the modulated spectrum (Eq. 4 with L = 0
+ * (Eq. 6) and J = f P^2 (Sec. VI)): for energy e,
+ *   J(T0) = (P0^2/beta0) (1/N) sum_b c_b w_b,  w_b = J_LIS(T_b) beta_b / P_b^2
+ * at the log-centre P_b of each bin; sigma = sample standard deviation of the
+ * summand / sqrt(N).  Only EXIT paths inside [P_min, P_max) enter N.
+ *   exit           device exit states (item = energy index)
+ *   T_in_GeVn      host [n_energies]
+ *   J_out, sigma_out  device [n_energies] (NaN where N = 0)
+ *   hist_out       device [n_energies * (nbins + 3)], overwritten
+ * The histogram is integer and order-independent, hence deterministic. */
+cosmica_status cosmica_spectrum(const cosmica_exit_states *exit, const cosmica_species *species,
+                                const double *T_in_GeVn, uint32_t n_energies,
+                                const cosmica_lis *lis, const cosmica_bins *bins,
+                                double *J_out, double *sigma_out, uint64_t *hist_out,
+                                void *stream);
+
+/* ---------------- batched persistent launch (many heliospheres) ---------------- */
+
+/* One work item: n quasi-particles of one species at one energy in one
+ * parameter set (the paper distributes energy bins over GPUs, Sec. IV.A; here
+ * many (set, species, energy) items share one persistent launch). */
+typedef struct {
+    uint32_t param_idx;       /* into the batch's parameter sets */
+    uint32_t species_idx;     /* into the batch's species        */
+    double T_GeVn;
+    uint32_t n;
+    uint32_t reserved;
+    uint64_t first_pid;
+    uint64_t seed;
+} cosmica_work_item;
+
+/* Launch shape of the persistent kernel; 0 fields select the defaults. */
+typedef struct {
+    uint32_t block;           /* threads per block                        */
+    uint32_t blocks_per_sm;   /* resident blocks per SM requested         */
+    uint32_t refill_batch;    /* lanes refilled per queue grab (1..32)    */
+    uint32_t use_graph;       /* 1: replay the launch as a CUDA graph     */
+} cosmica_tuning;
+
+typedef struct cosmica_batch cosmica_batch;
+
+/* Upload n_params parameter sets and n_species species (host) and derive
+ * their constants on the device.  All sets must share one precision (taken
+ * from params[0].precision). */
+cosmica_status cosmica_batch_create(const cosmica_params *params, uint32_t n_params,
+                                    const cosmica_species *species, uint32_t n_species,
+                                    cosmica_batch **out);
+void cosmica_batch_destroy(cosmica_batch *batch);
+
+/* Run every item of `items` (host, n_items) in one persistent launch fed by a
+ * device work queue.  Exit entry g belongs to the g-th particle in item order.
+ * `tuning` may be NULL.  If steps_out (device, 1 uint64) is not NULL it
+ * receives the total number of steps taken.  Errors: INVALID, OOM, CUDA. */
+cosmica_status cosmica_batch_run(cosmica_batch *batch, const cosmica_work_item *items,
+                                 uint32_t n_items, const cosmica_tuning *tuning,
+                                 cosmica_exit_states *out, uint64_t *steps_out, void *stream);
+
+/* Histogram and spectrum per work item of a batch run (same estimator as
+ * cosmica_spectrum; item k uses its own species and energy).  J_out,
+ * sigma_out: device [n_items]; hist_out: device [n_items * (nbins + 3)]. */
+cosmica_status cosmica_batch_spectrum(cosmica_batch *batch, const cosmica_work_item *items,
+                                      uint32_t n_items, const cosmica_exit_states *exit,
+                                      const cosmica_lis *lis, const cosmica_bins *bins,
+                                      double *J_out, double *sigma_out, uint64_t *hist_out,
+                                      void *stream);
+
+/* Pick a launch shape for this batch by timing candidate shapes on a short
+ * sample of `items` (host) and write the fastest to *best (steps/s in
+ * *best_rate if not NULL).  Synchronous; uses the batch's own scratch. */
+cosmica_status cosmica_autotune(cosmica_batch *batch, const cosmica_work_item *items,
+                                uint32_t n_items, cosmica_tuning *best, double *best_rate);
+
+/* Thread-local text of the last error of this thread ("" if none). */
+const char *cosmica_last_error(void);
+
+/* Number of device kernels this library has launched since load (all
+ * threads); lets callers count launches in a timed region. */
+uint64_t cosmica_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COSMICA_H */

@@ -1,0 +1,94 @@
+// common.cuh -- device-side records shared by the kernels of libcosmica.
+//
+// DevParams holds one heliosphere (one cosmica_params) twice: the raw FP64
+// values, from which the FP64 step derives every quantity in the same order
+// as its definition, and a block of FP32 constants pre-derived for the mixed
+// step.  The derived block is filled on the device by k_derive (FP64 unit,
+// deterministic elementary functions) so that host and device never disagree
+// on a constant.
+#pragma once
+#include <cstdint>
+
+#include "cosmica.h"
+
+namespace cosmica {
+
+constexpr double kPi = 3.141592653589793;
+constexpr double kTwoPi = 6.283185307179586;
+constexpr double kAU_m = 1.495978707e11;   // metres per AU
+constexpr double kAU_km = 1.495978707e8;   // kilometres per AU
+constexpr double kDay_s = 86400.0;         // seconds per day
+constexpr double kC_ms = 299792458.0;      // speed of light
+constexpr double kDeg = 0.017453292519943295;
+constexpr double kLn10 = 2.302585092994046;
+
+// FP32 constants of one heliosphere for the mixed-precision step.  The
+// isotropic model is expressed through the same fields (Omega = 0,
+// kperp fractions 1, one wind speed, no drift), so the step has no branch on it.
+struct alignas(16) F32Params {
+    float Vs, dV;              // slow wind and (fast - slow) [AU/day]
+    float lat_f, inv_dlat;     // transition latitude [rad], 1/width [1/rad]
+    float Omega;               // rotation rate [rad/day] (0 for isotropic)
+    float K0;                  // AU^2/day
+    float er, et;              // perpendicular fractions
+    float ts_drop, R_ts, inv_dts;   // termination shock (ts_drop = 0: none)
+    float r_in;
+    float dt_max, dt_fixed, dt_min;
+    float eps_adv2, eps_diff;  // 2 eps_adv, eps_diff
+    float CA0;                 // kappa_A prefactor: C_A = CA0 * beta * P  [AU^2/day]
+    float D2;                  // 2 r_L / r = D2 * P * r / sqrt(1 + Gamma^2)
+    float dcs_min;             // sheet half-width floor [rad]
+    float ta, ta2;             // tan(tilt), tan^2(tilt)
+    float polarity;            // +1 / -1
+    float drift, hcs;          // 0 / 1
+    float sqrt2er;             // sqrt(2 er)
+    float pad0, pad1;
+};
+
+struct DevParams {
+    // raw values (FP64 step)
+    double K0, er, et, B1AU, Vs_kms, Vf_kms, lat_fast_deg, tilt_deg, polarity;
+    double drift_on, hcs_on, isotropic;
+    double R_out, R_ts, ts_f, r_in, dt_max, dt_fixed, dt_min, eps_adv, eps_diff;
+    double V_const_kms, dlat_deg, dts, dcs_min_deg, rot_period, r0, th0, ph0, max_steps;
+    int32_t precision, pad;
+    // derived on the device
+    double B0;                 // nT, |B|(1 AU, equator) = B1AU
+    F32Params f;
+};
+
+struct DevSpecies {
+    double A, Z, m0;           // as doubles, the FP64 step's arithmetic type
+    float aoz_m0_sq;           // (A/|Z| m0)^2 [GV^2] for beta = P / sqrt(P^2 + M^2)
+    float sgnq;                // sign of the charge
+    float aoz;                 // A/|Z|
+    float pad;
+};
+
+struct DevItem {
+    double T;                  // GeV/n
+    uint64_t first_pid;
+    uint64_t seed;
+    uint32_t param_idx, species_idx;
+};
+
+struct ExitPtrs {
+    double *r, *th, *ph, *lnP, *s;
+    uint32_t *steps;
+    uint8_t *status;
+    uint32_t *item;
+};
+
+// Index of the work item owning global particle g: prefix[i] <= g < prefix[i+1].
+__device__ __forceinline__ uint32_t find_item(const uint64_t *__restrict__ prefix, uint32_t n_items,
+                                              uint64_t g)
+{
+    uint32_t lo = 0, hi = n_items;        // invariant: prefix[lo] <= g < prefix[hi]
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace cosmica

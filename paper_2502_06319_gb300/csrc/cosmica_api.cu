@@ -1,0 +1,916 @@
+// cosmica_api.cu -- the C ABI of libcosmica (cosmica.h, cosmica_debug.h).
+//
+// Host-side responsibilities only: argument validation, packing of the small
+// per-call tables (species, work items, prefix sums) into pinned staging
+// memory, their asynchronous upload into device scratch owned by the handle,
+// kernel launches on the caller's stream, staging of host-resident exit
+// buffers, CUDA-graph capture of repeated batched launches, and the launch
+// shape autotuner.  Every numeric step of the path runs in the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "cosmica.h"
+#include "cosmica_debug.h"
+#include "internal.h"
+
+using namespace cosmica;
+
+// ------------------------------------------------------------------ errors --
+namespace {
+thread_local char g_err[512] = "";
+std::atomic<unsigned long long> g_launches{0};
+
+cosmica_status fail(cosmica_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+cosmica_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(COSMICA_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(COSMICA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Grow-only device buffer.  cudaFree synchronises the device, so a buffer is
+// never released while a kernel that uses it is in flight.
+struct DevBuf {
+    void *d = nullptr;
+    size_t cap = 0;
+    cosmica_status reserve(size_t n)
+    {
+        if (n <= cap) return COSMICA_OK;
+        if (d) cudaFree(d);
+        d = nullptr;
+        cap = 0;
+        size_t want = std::max<size_t>(n, 4096);
+        cudaError_t e = cudaMalloc(&d, want);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(scratch)");
+        cap = want;
+        return COSMICA_OK;
+    }
+    void release()
+    {
+        if (d) cudaFree(d);
+        d = nullptr;
+        cap = 0;
+    }
+};
+
+// Pinned staging buffer for the small per-call tables.  Before it is
+// rewritten, the host waits for the previous upload from it to complete.
+struct Staging {
+    void *h = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+    cosmica_status reserve(size_t n)
+    {
+        if (pending) {
+            cudaError_t e = cudaEventSynchronize(ev);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize(staging)");
+            pending = false;
+        }
+        if (!ev) {
+            cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        }
+        if (n <= cap) return COSMICA_OK;
+        if (h) cudaFreeHost(h);
+        h = nullptr;
+        cap = 0;
+        size_t want = std::max<size_t>(n, 4096);
+        cudaError_t e = cudaMallocHost(&h, want);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost(staging)");
+        cap = want;
+        return COSMICA_OK;
+    }
+    cosmica_status upload(void *dst, size_t n, cudaStream_t s)
+    {
+        CK(cudaMemcpyAsync(dst, h, n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(tables)");
+        CK(cudaEventRecord(ev, s), "cudaEventRecord(staging)");
+        pending = true;
+        return COSMICA_OK;
+    }
+    void release()
+    {
+        if (pending && ev) cudaEventSynchronize(ev);
+        if (h) cudaFreeHost(h);
+        if (ev) cudaEventDestroy(ev);
+        h = nullptr;
+        ev = nullptr;
+        cap = 0;
+        pending = false;
+    }
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cosmica_status check_params(const cosmica_params *p)
+{
+    if (!p) return fail(COSMICA_ERR_INVALID, "params is NULL");
+    if (p->struct_size != sizeof(cosmica_params))
+        return fail(COSMICA_ERR_INVALID, "params.struct_size %u != %zu", p->struct_size, sizeof(cosmica_params));
+    if (p->version != COSMICA_ABI_VERSION)
+        return fail(COSMICA_ERR_INVALID, "params.version %u != %u", p->version, COSMICA_ABI_VERSION);
+    auto pos = [](double x) { return std::isfinite(x) && x > 0.0; };
+    if (!pos(p->K0)) return fail(COSMICA_ERR_INVALID, "K0 must be > 0");
+    if (!(p->r_in_AU > 0.0 && p->r0_AU >= p->r_in_AU && p->R_out_AU > p->r0_AU))
+        return fail(COSMICA_ERR_INVALID, "need 0 < r_in <= r0 < R_out");
+    if (!(p->th0_rad > 0.0 && p->th0_rad < kPi)) return fail(COSMICA_ERR_INVALID, "th0 must lie in (0, pi)");
+    if (!(p->dt_fixed_day > 0.0) && !(pos(p->dt_max_day) && pos(p->dt_min_day) && p->dt_min_day <= p->dt_max_day))
+        return fail(COSMICA_ERR_INVALID, "need dt_fixed > 0 or 0 < dt_min <= dt_max");
+    if (p->max_steps < 1) return fail(COSMICA_ERR_INVALID, "max_steps must be >= 1");
+    if (p->precision < COSMICA_PREC_FP64 || p->precision > COSMICA_PREC_MIXED_F64ACC)
+        return fail(COSMICA_ERR_INVALID, "unknown precision %d", p->precision);
+    if (!p->isotropic) {
+        if (!(pos(p->V_slow_kms) && pos(p->V_fast_kms) && pos(p->B1AU_nT) && pos(p->rot_period_day) &&
+              pos(p->dlat_deg)))
+            return fail(COSMICA_ERR_INVALID, "wind, field, rotation and transition widths must be > 0");
+        if (!(p->kperp_r_frac > 0.0 && p->kperp_th_frac > 0.0))
+            return fail(COSMICA_ERR_INVALID, "perpendicular diffusion fractions must be > 0");
+        if (p->polarity != 1 && p->polarity != -1) return fail(COSMICA_ERR_INVALID, "polarity must be +-1");
+        if (p->hcs_on && !(std::fabs(p->tilt_deg) < 89.0 && pos(p->dcs_min_deg)))
+            return fail(COSMICA_ERR_INVALID, "need |tilt| < 89 deg and dcs_min > 0");
+        if (p->R_ts_AU > 0.0 && !(pos(p->dts_AU) && p->ts_K_factor > 0.0))
+            return fail(COSMICA_ERR_INVALID, "termination shock needs dts > 0 and ts_K_factor > 0");
+    } else if (!(p->V_const_kms >= 0.0)) {
+        return fail(COSMICA_ERR_INVALID, "V_const must be >= 0");
+    }
+    return COSMICA_OK;
+}
+
+cosmica_status check_species(const cosmica_species *s)
+{
+    if (!s) return fail(COSMICA_ERR_INVALID, "species is NULL");
+    if (s->A < 1 || s->Z == 0 || !(s->m0_GeV > 0.0))
+        return fail(COSMICA_ERR_INVALID, "species needs A >= 1, Z != 0, m0 > 0");
+    return COSMICA_OK;
+}
+
+DevParams to_dev(const cosmica_params &p)
+{
+    DevParams d;
+    std::memset(&d, 0, sizeof(d));
+    d.K0 = p.K0; d.er = p.kperp_r_frac; d.et = p.kperp_th_frac; d.B1AU = p.B1AU_nT;
+    d.Vs_kms = p.V_slow_kms; d.Vf_kms = p.V_fast_kms; d.lat_fast_deg = p.lat_fast_deg;
+    d.tilt_deg = p.tilt_deg; d.polarity = (double)p.polarity;
+    d.drift_on = p.drift_on ? 1.0 : 0.0; d.hcs_on = p.hcs_on ? 1.0 : 0.0; d.isotropic = p.isotropic ? 1.0 : 0.0;
+    d.R_out = p.R_out_AU; d.R_ts = p.R_ts_AU; d.ts_f = p.ts_K_factor; d.r_in = p.r_in_AU;
+    d.dt_max = p.dt_max_day; d.dt_fixed = p.dt_fixed_day; d.dt_min = p.dt_min_day;
+    d.eps_adv = p.eps_adv; d.eps_diff = p.eps_diff; d.V_const_kms = p.V_const_kms;
+    d.dlat_deg = p.dlat_deg; d.dts = p.dts_AU; d.dcs_min_deg = p.dcs_min_deg; d.rot_period = p.rot_period_day;
+    d.r0 = p.r0_AU; d.th0 = p.th0_rad; d.ph0 = p.ph0_rad; d.max_steps = (double)p.max_steps;
+    d.precision = p.precision;
+    return d;
+}
+
+DevSpecies to_dev(const cosmica_species &s)
+{
+    DevSpecies d;
+    d.A = (double)s.A;
+    d.Z = (double)s.Z;
+    d.m0 = s.m0_GeV;
+    const double aoz = (double)s.A / std::fabs((double)s.Z);
+    d.aoz = (float)aoz;
+    d.aoz_m0_sq = (float)(aoz * s.m0_GeV * aoz * s.m0_GeV);
+    d.sgnq = s.Z > 0 ? 1.0f : -1.0f;
+    d.pad = 0.0f;
+    return d;
+}
+
+bool valid_exit(const cosmica_exit_states *o)
+{
+    return o && o->r && o->th && o->ph && o->lnP && o->s && o->steps && o->status && o->item;
+}
+
+ExitPtrs exit_ptrs(const cosmica_exit_states *o)
+{
+    return ExitPtrs{o->r, o->th, o->ph, o->lnP, o->s, o->steps, o->status, o->item};
+}
+
+// Device exit buffers standing in for host-resident outputs.
+struct ExitStage {
+    DevBuf buf;
+    cosmica_status make(uint64_t n, ExitPtrs &d)
+    {
+        const size_t per = 5 * sizeof(double) + 2 * sizeof(uint32_t) + 1;
+        cosmica_status st = buf.reserve(align_up(n * per + 64 * 8, 256));
+        if (st != COSMICA_OK) return st;
+        char *p = (char *)buf.d;
+        auto take = [&](size_t bytes) { char *q = p; p += align_up(bytes, 256); return q; };
+        d.r = (double *)take(n * 8); d.th = (double *)take(n * 8); d.ph = (double *)take(n * 8);
+        d.lnP = (double *)take(n * 8); d.s = (double *)take(n * 8);
+        d.steps = (uint32_t *)take(n * 4); d.item = (uint32_t *)take(n * 4); d.status = (uint8_t *)take(n);
+        return COSMICA_OK;
+    }
+    static cosmica_status copy_back(const ExitPtrs &d, const cosmica_exit_states *o, cudaStream_t s)
+    {
+        const uint64_t n = o->n;
+        CK(cudaMemcpyAsync(o->r, d.r, n * 8, cudaMemcpyDeviceToHost, s), "D2H r");
+        CK(cudaMemcpyAsync(o->th, d.th, n * 8, cudaMemcpyDeviceToHost, s), "D2H th");
+        CK(cudaMemcpyAsync(o->ph, d.ph, n * 8, cudaMemcpyDeviceToHost, s), "D2H ph");
+        CK(cudaMemcpyAsync(o->lnP, d.lnP, n * 8, cudaMemcpyDeviceToHost, s), "D2H lnP");
+        CK(cudaMemcpyAsync(o->s, d.s, n * 8, cudaMemcpyDeviceToHost, s), "D2H s");
+        CK(cudaMemcpyAsync(o->steps, d.steps, n * 4, cudaMemcpyDeviceToHost, s), "D2H steps");
+        CK(cudaMemcpyAsync(o->item, d.item, n * 4, cudaMemcpyDeviceToHost, s), "D2H item");
+        CK(cudaMemcpyAsync(o->status, d.status, n, cudaMemcpyDeviceToHost, s), "D2H status");
+        CK(cudaStreamSynchronize(s), "cudaStreamSynchronize(host exit states)");
+        return COSMICA_OK;
+    }
+};
+
+// Per-call tables: species/params are device-resident in the handle; items
+// and prefix sums are uploaded each call into `tables`.
+struct Tables {
+    DevBuf dev;
+    Staging stage;
+    DevItem *items = nullptr;
+    uint64_t *prefix = nullptr;
+    unsigned long long *counters = nullptr;   // [0] cursor, [1] steps
+    uint64_t n_total = 0;
+    uint32_t n_items = 0;
+
+    cosmica_status build(const std::vector<DevItem> &its, const std::vector<uint64_t> &pre, cudaStream_t s)
+    {
+        const size_t nI = its.size();
+        const size_t b_items = align_up(nI * sizeof(DevItem), 256);
+        const size_t b_pre = align_up((nI + 1) * sizeof(uint64_t), 256);
+        const size_t total = b_items + b_pre + 256;
+        cosmica_status st = dev.reserve(total);
+        if (st != COSMICA_OK) return st;
+        st = stage.reserve(b_items + b_pre);
+        if (st != COSMICA_OK) return st;
+        std::memcpy(stage.h, its.data(), nI * sizeof(DevItem));
+        std::memcpy((char *)stage.h + b_items, pre.data(), (nI + 1) * sizeof(uint64_t));
+        items = (DevItem *)dev.d;
+        prefix = (uint64_t *)((char *)dev.d + b_items);
+        counters = (unsigned long long *)((char *)dev.d + b_items + b_pre);
+        n_items = (uint32_t)nI;
+        n_total = pre[nI];
+        return stage.upload(dev.d, b_items + b_pre, s);
+    }
+    void release()
+    {
+        stage.release();
+        dev.release();
+    }
+};
+
+int g_num_sms = 0;
+int num_sms()
+{
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+PersistentShape shape_for(int acc, const cosmica_tuning *t, uint64_t n_total)
+{
+    unsigned block = (t && t->block) ? t->block : 128u;
+    block = std::min(256u, std::max(32u, block / 32u * 32u));
+    int max_b = mixed_max_blocks_per_sm(acc, block);
+    if (max_b < 1) max_b = 1;
+    int bps = (t && t->blocks_per_sm) ? (int)t->blocks_per_sm : max_b;
+    bps = std::min(bps, max_b);
+    uint64_t grid = (uint64_t)num_sms() * (uint64_t)bps;
+    const uint64_t need = (n_total + block - 1) / block;   // never more blocks than particles
+    grid = std::max<uint64_t>(1, std::min(grid, need));
+    return PersistentShape{block, (unsigned)grid};
+}
+
+}  // namespace
+
+namespace cosmica {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace cosmica
+
+// =============================================================== model API ==
+struct cosmica_model {
+    cosmica_params p;
+    DevParams *d_prm = nullptr;
+    DevBuf spc;                 // DevSpecies[1] + spectrum items
+    Staging spc_stage;
+    Tables tab;
+    ExitStage exit_stage;
+    DevBuf spec_items;
+    Staging spec_stage;
+    DevBuf lis_buf;
+    Staging lis_stage;
+    DevBuf dbg;
+};
+
+extern "C" void cosmica_params_default(cosmica_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->struct_size = sizeof(cosmica_params);
+    p->version = COSMICA_ABI_VERSION;
+    p->K0 = 11.5;
+    p->kperp_r_frac = 0.02;
+    p->kperp_th_frac = 0.02;
+    p->B1AU_nT = 5.0;
+    p->V_slow_kms = 400.0;
+    p->V_fast_kms = 760.0;
+    p->lat_fast_deg = 30.0;
+    p->tilt_deg = 20.0;
+    p->polarity = 1;
+    p->drift_on = 1;
+    p->hcs_on = 1;
+    p->isotropic = 0;
+    p->R_out_AU = 100.0;
+    p->R_ts_AU = 0.0;
+    p->ts_K_factor = 0.5;
+    p->r_in_AU = 0.1;
+    p->dt_max_day = 0.1;
+    p->dt_fixed_day = 0.0;
+    p->dt_min_day = 1e-4;
+    p->eps_adv = 0.01;
+    p->eps_diff = 0.01;
+    p->V_const_kms = 400.0;
+    p->dlat_deg = 2.0;
+    p->dts_AU = 1.0;
+    p->dcs_min_deg = 1.0;
+    p->rot_period_day = 25.38;
+    p->r0_AU = 1.0;
+    p->th0_rad = kPi / 2.0;
+    p->ph0_rad = 0.0;
+    p->max_steps = 100000000u;
+    p->precision = COSMICA_PREC_FP64;
+}
+
+static cosmica_status upload_params(const cosmica_params *ps, uint32_t n, DevParams **out)
+{
+    std::vector<DevParams> h(n);
+    for (uint32_t i = 0; i < n; ++i) h[i] = to_dev(ps[i]);
+    DevParams *d = nullptr;
+    CK(cudaMalloc(&d, n * sizeof(DevParams)), "cudaMalloc(params)");
+    cudaError_t e = cudaMemcpy(d, h.data(), n * sizeof(DevParams), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_derive(d, n, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "deriving parameter constants");
+    }
+    *out = d;
+    return COSMICA_OK;
+}
+
+extern "C" cosmica_status cosmica_model_create(const cosmica_params *params, cosmica_model **out)
+{
+    if (!out) return fail(COSMICA_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    cosmica_status st = check_params(params);
+    if (st != COSMICA_OK) return st;
+    cosmica_model *m = new (std::nothrow) cosmica_model();
+    if (!m) return fail(COSMICA_ERR_OOM, "host allocation of the model");
+    m->p = *params;
+    st = upload_params(params, 1, &m->d_prm);
+    if (st != COSMICA_OK) {
+        delete m;
+        return st;
+    }
+    *out = m;
+    return COSMICA_OK;
+}
+
+extern "C" void cosmica_model_destroy(cosmica_model *m)
+{
+    if (!m) return;
+    cudaDeviceSynchronize();
+    if (m->d_prm) cudaFree(m->d_prm);
+    m->spc.release();
+    m->spc_stage.release();
+    m->tab.release();
+    m->exit_stage.buf.release();
+    m->spec_items.release();
+    m->spec_stage.release();
+    m->lis_buf.release();
+    m->lis_stage.release();
+    m->dbg.release();
+    delete m;
+}
+
+static cosmica_status upload_species(DevBuf &buf, Staging &stage, const cosmica_species *sp, uint32_t n,
+                                     cudaStream_t s, DevSpecies **out)
+{
+    cosmica_status st = buf.reserve(n * sizeof(DevSpecies));
+    if (st != COSMICA_OK) return st;
+    st = stage.reserve(n * sizeof(DevSpecies));
+    if (st != COSMICA_OK) return st;
+    for (uint32_t i = 0; i < n; ++i) ((DevSpecies *)stage.h)[i] = to_dev(sp[i]);
+    st = stage.upload(buf.d, n * sizeof(DevSpecies), s);
+    if (st != COSMICA_OK) return st;
+    *out = (DevSpecies *)buf.d;
+    return COSMICA_OK;
+}
+
+extern "C" cosmica_status cosmica_propagate(cosmica_model *m, const cosmica_species *species,
+                                            const double *T_in, uint32_t n_energies, const uint32_t *n_per_energy,
+                                            uint64_t seed, cosmica_exit_states *out, void *stream)
+{
+    if (!m) return fail(COSMICA_ERR_INVALID, "model is NULL");
+    cosmica_status st = check_species(species);
+    if (st != COSMICA_OK) return st;
+    if (n_energies > 0 && (!T_in || !n_per_energy)) return fail(COSMICA_ERR_INVALID, "T_in / n_per_energy NULL");
+    if (!out) return fail(COSMICA_ERR_INVALID, "out is NULL");
+    uint64_t total = 0;
+    for (uint32_t e = 0; e < n_energies; ++e) {
+        if (!(std::isfinite(T_in[e]) && T_in[e] > 0.0)) return fail(COSMICA_ERR_INVALID, "T_in[%u] must be > 0", e);
+        total += n_per_energy[e];
+    }
+    if (out->n != total) return fail(COSMICA_ERR_INVALID, "out->n = %llu, sum(n_per_energy) = %llu",
+                                     (unsigned long long)out->n, (unsigned long long)total);
+    if (total == 0) return COSMICA_OK;
+    if (!valid_exit(out)) return fail(COSMICA_ERR_INVALID, "exit-state arrays must be non-NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+
+    DevSpecies *d_sp = nullptr;
+    st = upload_species(m->spc, m->spc_stage, species, 1, s, &d_sp);
+    if (st != COSMICA_OK) return st;
+    std::vector<DevItem> its(n_energies);
+    std::vector<uint64_t> pre(n_energies + 1, 0);
+    for (uint32_t e = 0; e < n_energies; ++e) {
+        its[e].T = T_in[e];
+        its[e].first_pid = pre[e];
+        its[e].seed = seed;
+        its[e].param_idx = 0;
+        its[e].species_idx = 0;
+        pre[e + 1] = pre[e] + n_per_energy[e];
+    }
+    st = m->tab.build(its, pre, s);
+    if (st != COSMICA_OK) return st;
+
+    const bool host_out = !is_device_ptr(out->r);
+    ExitPtrs ex = exit_ptrs(out);
+    if (host_out) {
+        st = m->exit_stage.make(total, ex);
+        if (st != COSMICA_OK) return st;
+    }
+    CK(cudaMemsetAsync(m->tab.counters, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
+    LaunchArgs a{m->d_prm, d_sp, m->tab.items, m->tab.prefix, m->tab.n_items, total, ex,
+                 m->tab.counters + 1, m->tab.counters};
+    cudaError_t e;
+    if (m->p.precision == COSMICA_PREC_FP64) {
+        e = launch_propagate_fp64(a, s);
+    } else {
+        e = launch_propagate_mixed(a, m->p.precision, shape_for(m->p.precision, nullptr, total), s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
+    if (host_out) return ExitStage::copy_back(ex, out, s);
+    return COSMICA_OK;
+}
+
+// ============================================================ spectrum API ==
+static cosmica_status check_bins(const cosmica_bins *b, double *x_lo, double *dx)
+{
+    if (!b) return fail(COSMICA_ERR_INVALID, "bins is NULL");
+    if (!(b->P_min_GV > 0.0 && b->P_max_GV > b->P_min_GV && b->nbins >= 1))
+        return fail(COSMICA_ERR_INVALID, "need 0 < P_min < P_max and nbins >= 1");
+    *x_lo = std::log10(b->P_min_GV);
+    *dx = (std::log10(b->P_max_GV) - *x_lo) / (double)b->nbins;
+    return COSMICA_OK;
+}
+
+static cosmica_status upload_lis(const cosmica_lis *lis, DevBuf &buf, Staging &stage, cudaStream_t s,
+                                 int *kind, const double **lnT, const double **lnJ, uint32_t *n)
+{
+    *kind = 0; *lnT = nullptr; *lnJ = nullptr; *n = 0;
+    if (!lis || lis->kind == 0) return COSMICA_OK;
+    if (lis->kind != 1 || lis->n < 2 || !lis->lnT || !lis->lnJ)
+        return fail(COSMICA_ERR_INVALID, "LIS table needs kind 1, n >= 2 and both arrays");
+    for (uint32_t i = 1; i < lis->n; ++i)
+        if (!(lis->lnT[i] > lis->lnT[i - 1])) return fail(COSMICA_ERR_INVALID, "LIS lnT must ascend");
+    const size_t bytes = 2 * lis->n * sizeof(double);
+    cosmica_status st = buf.reserve(bytes);
+    if (st != COSMICA_OK) return st;
+    st = stage.reserve(bytes);
+    if (st != COSMICA_OK) return st;
+    std::memcpy(stage.h, lis->lnT, lis->n * sizeof(double));
+    std::memcpy((double *)stage.h + lis->n, lis->lnJ, lis->n * sizeof(double));
+    st = stage.upload(buf.d, bytes, s);
+    if (st != COSMICA_OK) return st;
+    *kind = 1;
+    *lnT = (const double *)buf.d;
+    *lnJ = (const double *)buf.d + lis->n;
+    *n = lis->n;
+    return COSMICA_OK;
+}
+
+static cosmica_status run_spectrum(const cosmica_exit_states *ex, const std::vector<SpecItem> &its,
+                                   const cosmica_lis *lis, const cosmica_bins *bins, double *J, double *sigma,
+                                   uint64_t *hist, DevBuf &ibuf, Staging &istage, DevBuf &lbuf, Staging &lstage,
+                                   cudaStream_t s)
+{
+    double x_lo, dx;
+    cosmica_status st = check_bins(bins, &x_lo, &dx);
+    if (st != COSMICA_OK) return st;
+    const uint32_t n_items = (uint32_t)its.size();
+    if (n_items == 0) return COSMICA_OK;
+    if (!J || !sigma || !hist) return fail(COSMICA_ERR_INVALID, "J / sigma / hist must be non-NULL");
+    if (!ex) return fail(COSMICA_ERR_INVALID, "exit states NULL");
+    if (ex->n > 0 && !valid_exit(ex)) return fail(COSMICA_ERR_INVALID, "exit-state arrays must be non-NULL");
+    if (ex->n > 0 && !is_device_ptr(ex->lnP)) return fail(COSMICA_ERR_INVALID, "exit states must be device memory");
+    if (!is_device_ptr(J) || !is_device_ptr(sigma) || !is_device_ptr(hist))
+        return fail(COSMICA_ERR_INVALID, "J / sigma / hist must be device memory");
+    const size_t hbytes = (size_t)n_items * COSMICA_HIST_STRIDE(bins->nbins) * sizeof(uint64_t);
+    CK(cudaMemsetAsync(hist, 0, hbytes, s), "cudaMemsetAsync(hist)");
+    cudaError_t e = launch_histogram(exit_ptrs(ex), ex->n, n_items, bins->nbins, x_lo, dx,
+                                     (unsigned long long *)hist, s);
+    if (e != cudaSuccess) return cuda_fail(e, "histogram kernel launch");
+    st = ibuf.reserve(n_items * sizeof(SpecItem));
+    if (st != COSMICA_OK) return st;
+    st = istage.reserve(n_items * sizeof(SpecItem));
+    if (st != COSMICA_OK) return st;
+    std::memcpy(istage.h, its.data(), n_items * sizeof(SpecItem));
+    st = istage.upload(ibuf.d, n_items * sizeof(SpecItem), s);
+    if (st != COSMICA_OK) return st;
+    int kind; const double *lnT, *lnJ; uint32_t ln;
+    st = upload_lis(lis, lbuf, lstage, s, &kind, &lnT, &lnJ, &ln);
+    if (st != COSMICA_OK) return st;
+    e = launch_spectrum((const unsigned long long *)hist, n_items, bins->nbins, x_lo, dx, (const SpecItem *)ibuf.d,
+                        kind, lnT, lnJ, ln, J, sigma, s);
+    if (e != cudaSuccess) return cuda_fail(e, "spectrum kernel launch");
+    return COSMICA_OK;
+}
+
+extern "C" cosmica_status cosmica_spectrum(const cosmica_exit_states *exit, const cosmica_species *species,
+                                           const double *T_in, uint32_t n_energies, const cosmica_lis *lis,
+                                           const cosmica_bins *bins, double *J_out, double *sigma_out,
+                                           uint64_t *hist_out, void *stream)
+{
+    cosmica_status st = check_species(species);
+    if (st != COSMICA_OK) return st;
+    if (n_energies > 0 && !T_in) return fail(COSMICA_ERR_INVALID, "T_in is NULL");
+    std::vector<SpecItem> its(n_energies);
+    for (uint32_t e = 0; e < n_energies; ++e)
+        its[e] = SpecItem{T_in[e], (double)species->A, (double)species->Z, species->m0_GeV};
+    // scratch of the calling thread: the spectrum call carries no handle
+    thread_local DevBuf ibuf, lbuf;
+    thread_local Staging istage, lstage;
+    return run_spectrum(exit, its, lis, bins, J_out, sigma_out, hist_out, ibuf, istage, lbuf, lstage,
+                        (cudaStream_t)stream);
+}
+
+// =============================================================== batch API ==
+struct cosmica_batch {
+    std::vector<cosmica_params> params;
+    std::vector<cosmica_species> species;
+    int precision = 0;
+    DevParams *d_prm = nullptr;
+    DevSpecies *d_spc = nullptr;
+    Tables tab;
+    ExitStage exit_stage;
+    DevBuf spec_items, lis_buf;
+    Staging spec_stage, lis_stage;
+    // CUDA graph of [memset counters, persistent kernel] for repeated runs
+    cudaGraphExec_t gexec = nullptr;
+    std::tuple<uint64_t, uint32_t, const void *, const void *, unsigned, unsigned, cudaStream_t, int> gkey{};
+};
+
+extern "C" cosmica_status cosmica_batch_create(const cosmica_params *params, uint32_t n_params,
+                                               const cosmica_species *species, uint32_t n_species,
+                                               cosmica_batch **out)
+{
+    if (!out) return fail(COSMICA_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n_params == 0 || n_species == 0 || !params || !species)
+        return fail(COSMICA_ERR_INVALID, "need at least one parameter set and one species");
+    for (uint32_t i = 0; i < n_params; ++i) {
+        cosmica_status st = check_params(params + i);
+        if (st != COSMICA_OK) return st;
+        if (params[i].precision != params[0].precision)
+            return fail(COSMICA_ERR_INVALID, "all parameter sets of a batch must share one precision");
+    }
+    for (uint32_t i = 0; i < n_species; ++i) {
+        cosmica_status st = check_species(species + i);
+        if (st != COSMICA_OK) return st;
+    }
+    cosmica_batch *b = new (std::nothrow) cosmica_batch();
+    if (!b) return fail(COSMICA_ERR_OOM, "host allocation of the batch");
+    b->params.assign(params, params + n_params);
+    b->species.assign(species, species + n_species);
+    b->precision = params[0].precision;
+    cosmica_status st = upload_params(params, n_params, &b->d_prm);
+    if (st == COSMICA_OK) {
+        std::vector<DevSpecies> hs(n_species);
+        for (uint32_t i = 0; i < n_species; ++i) hs[i] = to_dev(species[i]);
+        cudaError_t e = cudaMalloc(&b->d_spc, n_species * sizeof(DevSpecies));
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_spc, hs.data(), n_species * sizeof(DevSpecies), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_fail(e, "species upload");
+    }
+    if (st != COSMICA_OK) {
+        cosmica_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return COSMICA_OK;
+}
+
+extern "C" void cosmica_batch_destroy(cosmica_batch *b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->d_prm) cudaFree(b->d_prm);
+    if (b->d_spc) cudaFree(b->d_spc);
+    b->tab.release();
+    b->exit_stage.buf.release();
+    b->spec_items.release();
+    b->lis_buf.release();
+    b->spec_stage.release();
+    b->lis_stage.release();
+    delete b;
+}
+
+static cosmica_status batch_items(const cosmica_batch *b, const cosmica_work_item *items, uint32_t n_items,
+                                  std::vector<DevItem> &its, std::vector<uint64_t> &pre)
+{
+    if (n_items > 0 && !items) return fail(COSMICA_ERR_INVALID, "items is NULL");
+    its.resize(n_items);
+    pre.assign(n_items + 1, 0);
+    for (uint32_t i = 0; i < n_items; ++i) {
+        const cosmica_work_item &w = items[i];
+        if (w.param_idx >= b->params.size() || w.species_idx >= b->species.size())
+            return fail(COSMICA_ERR_INVALID, "item %u: parameter or species index out of range", i);
+        if (!(std::isfinite(w.T_GeVn) && w.T_GeVn > 0.0)) return fail(COSMICA_ERR_INVALID, "item %u: T must be > 0", i);
+        its[i] = DevItem{w.T_GeVn, w.first_pid, w.seed, w.param_idx, w.species_idx};
+        pre[i + 1] = pre[i] + w.n;
+    }
+    return COSMICA_OK;
+}
+
+static cosmica_status batch_launch(cosmica_batch *b, uint64_t total, const ExitPtrs &ex,
+                                   const cosmica_tuning *tuning, cudaStream_t s)
+{
+    LaunchArgs a{b->d_prm, b->d_spc, b->tab.items, b->tab.prefix, b->tab.n_items, total, ex,
+                 b->tab.counters + 1, b->tab.counters};
+    auto direct = [&]() -> cosmica_status {
+        CK(cudaMemsetAsync(b->tab.counters, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
+        cudaError_t e = (b->precision == COSMICA_PREC_FP64)
+                            ? launch_propagate_fp64(a, s)
+                            : launch_propagate_mixed(a, b->precision, shape_for(b->precision, tuning, total), s);
+        if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
+        return COSMICA_OK;
+    };
+    const bool graph = tuning && tuning->use_graph && s != nullptr;
+    if (!graph) return direct();
+    const PersistentShape sh = shape_for(b->precision, tuning, total);
+    auto key = std::make_tuple(total, b->tab.n_items, (const void *)ex.r, (const void *)b->tab.dev.d, sh.block,
+                               sh.grid, s, b->precision);
+    if (!b->gexec || b->gkey != key) {
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        cosmica_status st = direct();
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st != COSMICA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->gexec = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        b->gkey = key;
+    }
+    CK(cudaGraphLaunch(b->gexec, s), "cudaGraphLaunch");
+    note_launch();
+    return COSMICA_OK;
+}
+
+extern "C" cosmica_status cosmica_batch_run(cosmica_batch *b, const cosmica_work_item *items, uint32_t n_items,
+                                            const cosmica_tuning *tuning, cosmica_exit_states *out,
+                                            uint64_t *steps_out, void *stream)
+{
+    if (!b) return fail(COSMICA_ERR_INVALID, "batch is NULL");
+    if (!out) return fail(COSMICA_ERR_INVALID, "out is NULL");
+    std::vector<DevItem> its;
+    std::vector<uint64_t> pre;
+    cosmica_status st = batch_items(b, items, n_items, its, pre);
+    if (st != COSMICA_OK) return st;
+    const uint64_t total = pre[n_items];
+    if (out->n != total) return fail(COSMICA_ERR_INVALID, "out->n = %llu, particles = %llu",
+                                     (unsigned long long)out->n, (unsigned long long)total);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (total == 0) {
+        if (steps_out) CK(cudaMemsetAsync(steps_out, 0, sizeof(uint64_t), s), "cudaMemsetAsync(steps)");
+        return COSMICA_OK;
+    }
+    if (!valid_exit(out)) return fail(COSMICA_ERR_INVALID, "exit-state arrays must be non-NULL");
+    st = b->tab.build(its, pre, s);
+    if (st != COSMICA_OK) return st;
+    const bool host_out = !is_device_ptr(out->r);
+    ExitPtrs ex = exit_ptrs(out);
+    if (host_out) {
+        st = b->exit_stage.make(total, ex);
+        if (st != COSMICA_OK) return st;
+    }
+    st = batch_launch(b, total, ex, tuning, s);
+    if (st != COSMICA_OK) return st;
+    if (steps_out)
+        CK(cudaMemcpyAsync(steps_out, b->tab.counters + 1, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s),
+           "copy steps");
+    if (host_out) return ExitStage::copy_back(ex, out, s);
+    return COSMICA_OK;
+}
+
+extern "C" cosmica_status cosmica_batch_spectrum(cosmica_batch *b, const cosmica_work_item *items,
+                                                 uint32_t n_items, const cosmica_exit_states *exit,
+                                                 const cosmica_lis *lis, const cosmica_bins *bins, double *J_out,
+                                                 double *sigma_out, uint64_t *hist_out, void *stream)
+{
+    if (!b) return fail(COSMICA_ERR_INVALID, "batch is NULL");
+    if (n_items > 0 && !items) return fail(COSMICA_ERR_INVALID, "items is NULL");
+    std::vector<SpecItem> its(n_items);
+    for (uint32_t i = 0; i < n_items; ++i) {
+        if (items[i].species_idx >= b->species.size()) return fail(COSMICA_ERR_INVALID, "species index out of range");
+        const cosmica_species &sp = b->species[items[i].species_idx];
+        its[i] = SpecItem{items[i].T_GeVn, (double)sp.A, (double)sp.Z, sp.m0_GeV};
+    }
+    return run_spectrum(exit, its, lis, bins, J_out, sigma_out, hist_out, b->spec_items, b->spec_stage,
+                        b->lis_buf, b->lis_stage, (cudaStream_t)stream);
+}
+
+// =============================================================== autotune ==
+extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_item *items, uint32_t n_items,
+                                           cosmica_tuning *best, double *best_rate)
+{
+    if (!b || !best) return fail(COSMICA_ERR_INVALID, "batch / best is NULL");
+    if (b->precision == COSMICA_PREC_FP64) {
+        *best = cosmica_tuning{128, 0, 1, 0};
+        if (best_rate) *best_rate = 0.0;
+        return COSMICA_OK;
+    }
+    std::vector<DevItem> its;
+    std::vector<uint64_t> pre;
+    cosmica_status st = batch_items(b, items, n_items, its, pre);
+    if (st != COSMICA_OK) return st;
+    if (pre[n_items] == 0) return fail(COSMICA_ERR_INVALID, "autotune needs particles");
+    // sample: every item scaled down so the sample holds ~6 particles per resident lane
+    const uint64_t lanes = (uint64_t)num_sms() * 2048u;
+    const double scale = std::min(1.0, 6.0 * (double)lanes / (double)pre[n_items]);
+    std::vector<cosmica_work_item> sample(items, items + n_items);
+    uint64_t total = 0;
+    for (auto &w : sample) {
+        w.n = (uint32_t)std::ceil(w.n * scale);
+        total += w.n;
+    }
+    DevBuf out_buf;
+    ExitPtrs ex;
+    {
+        ExitStage tmp;
+        st = tmp.make(total, ex);
+        if (st != COSMICA_OK) return st;
+        out_buf = tmp.buf;
+    }
+    cosmica_exit_states eo{ex.r, ex.th, ex.ph, ex.lnP, ex.s, ex.steps, ex.status, ex.item, total};
+    unsigned long long *d_steps = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaMalloc(&d_steps, sizeof(unsigned long long));
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    double best_r = -1.0;
+    cosmica_tuning bt{128, 0, 1, 0};
+    if (ce == cudaSuccess) {
+        const unsigned blocks[] = {64, 128, 256};
+        for (unsigned blk : blocks) {
+            const int maxb = mixed_max_blocks_per_sm(b->precision, blk);
+            for (int frac = 0; frac < 2; ++frac) {
+                const unsigned bps = frac == 0 ? (unsigned)std::max(1, maxb) : (unsigned)std::max(1, maxb / 2);
+                if (frac == 1 && bps == (unsigned)std::max(1, maxb)) continue;
+                cosmica_tuning t{blk, bps, 1, 0};
+                ce = cudaEventRecord(e0, s);
+                if (ce != cudaSuccess) break;
+                st = cosmica_batch_run(b, sample.data(), n_items, &t, &eo, (uint64_t *)d_steps, s);
+                if (st != COSMICA_OK) break;
+                ce = cudaEventRecord(e1, s);
+                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                if (ce != cudaSuccess) break;
+                float ms = 0.0f;
+                unsigned long long steps = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ce = cudaMemcpy(&steps, d_steps, sizeof(steps), cudaMemcpyDeviceToHost);
+                if (ce != cudaSuccess) break;
+                const double rate = ms > 0.0f ? (double)steps / (ms * 1e-3) : 0.0;
+                if (rate > best_r) {
+                    best_r = rate;
+                    bt = t;
+                }
+            }
+            if (st != COSMICA_OK || ce != cudaSuccess) break;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    if (d_steps) cudaFree(d_steps);
+    out_buf.release();
+    if (st != COSMICA_OK) return st;
+    if (ce != cudaSuccess) return cuda_fail(ce, "autotune");
+    *best = bt;
+    if (best_rate) *best_rate = best_r;
+    return COSMICA_OK;
+}
+
+// ================================================================== misc ==
+extern "C" const char *cosmica_last_error(void) { return g_err; }
+
+extern "C" uint64_t cosmica_launch_count(void) { return g_launches.load(); }
+
+// ================================================================= debug ==
+extern "C" cosmica_status cosmica_debug_philox(uint32_t n, const uint32_t *ctr, uint32_t k0, uint32_t k1,
+                                               uint32_t *out, void *stream)
+{
+    if (n && (!ctr || !out)) return fail(COSMICA_ERR_INVALID, "NULL array");
+    cudaError_t e = launch_debug_philox(n, ctr, k0, k1, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? COSMICA_OK : cuda_fail(e, "philox probe");
+}
+
+extern "C" cosmica_status cosmica_debug_curand_philox(uint32_t n, uint64_t seed, const uint64_t *subseq,
+                                                      const uint64_t *offset, uint32_t *out, void *stream)
+{
+    if (n && (!subseq || !offset || !out)) return fail(COSMICA_ERR_INVALID, "NULL array");
+    cudaError_t e = launch_debug_curand_philox(n, seed, (const unsigned long long *)subseq,
+                                               (const unsigned long long *)offset, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? COSMICA_OK : cuda_fail(e, "curand probe");
+}
+
+extern "C" cosmica_status cosmica_debug_normals64(uint64_t seed, uint64_t pid0, uint32_t n, uint32_t step,
+                                                  double *z, void *stream)
+{
+    if (n && !z) return fail(COSMICA_ERR_INVALID, "NULL array");
+    cudaError_t e = launch_debug_normals64(seed, pid0, n, step, z, (cudaStream_t)stream);
+    return e == cudaSuccess ? COSMICA_OK : cuda_fail(e, "normals probe");
+}
+
+extern "C" cosmica_status cosmica_debug_fn64(int32_t which, uint32_t n, const double *x, double *y, void *stream)
+{
+    if (which < 0 || which > 5) return fail(COSMICA_ERR_INVALID, "function code %d", which);
+    if (n && (!x || !y)) return fail(COSMICA_ERR_INVALID, "NULL array");
+    cudaError_t e = launch_debug_fn64(which, n, x, y, (cudaStream_t)stream);
+    return e == cudaSuccess ? COSMICA_OK : cuda_fail(e, "elementary-function probe");
+}
+
+extern "C" cosmica_status cosmica_debug_eval(cosmica_model *m, const cosmica_species *species, int32_t precision,
+                                             uint32_t n, const double *states, double *out, void *stream)
+{
+    if (!m) return fail(COSMICA_ERR_INVALID, "model is NULL");
+    cosmica_status st = check_species(species);
+    if (st != COSMICA_OK) return st;
+    if (n && (!states || !out)) return fail(COSMICA_ERR_INVALID, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevSpecies *d_sp = nullptr;
+    st = upload_species(m->spc, m->spc_stage, species, 1, s, &d_sp);
+    if (st != COSMICA_OK) return st;
+    cudaError_t e = precision == 0 ? launch_debug_eval64(m->d_prm, d_sp, n, states, out, s)
+                                   : launch_debug_eval32(m->d_prm, d_sp, n, states, out, s);
+    return e == cudaSuccess ? COSMICA_OK : cuda_fail(e, "evaluator probe");
+}

@@ -1,0 +1,63 @@
+// internal.h -- declarations shared by the translation units of libcosmica
+// (launchers implemented in the kernel files, called by the C-ABI layer).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace cosmica {
+
+constexpr int kDebugEvalN = 21;   // quantities written per state by the debug evaluators
+
+struct LaunchArgs {
+    const DevParams *prm;
+    const DevSpecies *spc;
+    const DevItem *items;
+    const uint64_t *prefix;
+    uint32_t n_items;
+    uint64_t n_total;
+    ExitPtrs out;
+    unsigned long long *steps_total;   // may be null
+    unsigned long long *cursor;        // work-queue cursor (persistent kernels)
+};
+
+struct PersistentShape {
+    unsigned block;
+    unsigned grid;
+};
+
+void note_launch();
+
+cudaError_t launch_derive(DevParams *prm, uint32_t n, cudaStream_t s);
+cudaError_t launch_propagate_fp64(const LaunchArgs &a, cudaStream_t s);
+
+// mixed precision persistent kernel; acc = COSMICA_PREC_MIXED or COSMICA_PREC_MIXED_F64ACC
+cudaError_t launch_propagate_mixed(const LaunchArgs &a, int acc, PersistentShape shape, cudaStream_t s);
+int mixed_max_blocks_per_sm(int acc, unsigned block);
+
+cudaError_t launch_histogram(const ExitPtrs &ex, uint64_t n, uint32_t n_items, uint32_t nbins, double x_lo,
+                             double dx, unsigned long long *hist, cudaStream_t s);
+struct SpecItem {
+    double T;                  // GeV/n
+    double A, Z, m0;           // species
+};
+cudaError_t launch_spectrum(const unsigned long long *hist, uint32_t n_items, uint32_t nbins,
+                            double x_lo, double dx, const SpecItem *items, int lis_kind,
+                            const double *lis_lnT, const double *lis_lnJ, uint32_t lis_n,
+                            double *J, double *sigma, cudaStream_t s);
+
+cudaError_t launch_debug_eval64(const DevParams *prm, const DevSpecies *spc, uint32_t n, const double *st,
+                                double *out, cudaStream_t s);
+cudaError_t launch_debug_eval32(const DevParams *prm, const DevSpecies *spc, uint32_t n, const double *st,
+                                double *out, cudaStream_t s);
+cudaError_t launch_debug_fn64(int which, uint32_t n, const double *x, double *y, cudaStream_t s);
+cudaError_t launch_debug_normals64(uint64_t seed, uint64_t pid0, uint32_t n, uint32_t step, double *z,
+                                   cudaStream_t s);
+cudaError_t launch_debug_philox(uint32_t n, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
+                                cudaStream_t s);
+cudaError_t launch_debug_curand_philox(uint32_t n, uint64_t seed, const unsigned long long *subseq,
+                                       const unsigned long long *offset, uint32_t *out, cudaStream_t s);
+
+}  // namespace cosmica

@@ -1,0 +1,266 @@
+// k_mixed.cu -- the batched persistent kernel of the mixed-precision path.
+//
+// One launch of (SMs x resident blocks) threads drains a device work queue:
+// an atomic cursor over the prefix-summed particle counts of all work items
+// (parameter set x species x energy).  Each lane owns one quasi-particle at a
+// time and steps it until it leaves the heliosphere; a lane whose particle
+// exits writes the exit state and immediately takes the next particle from
+// the queue (refill), so that warps stay full while the queue lasts despite
+// the long tail of exit times.  Lanes needing work in the same step take
+// consecutive particles with one atomic per warp.  The paper's thread-per-
+// quasi-particle mapping (Sec. IV.A) is kept; its one-launch-per-energy-bin
+// loop (Sec. IV.A, last paragraph) becomes this single launch.
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+#include "model32.cuh"
+
+namespace cosmica {
+
+namespace {
+
+struct Lane {
+    const F32Params *q;
+    float M2, sq;
+    uint64_t pid, seed, g;
+    uint32_t item, k, max_steps;
+    double R_out;
+};
+
+template <int ACC>
+struct Acc;
+
+// compensated FP32 state
+template <>
+struct Acc<COSMICA_PREC_MIXED> {
+    m32::FF r, th, ph, lnP, s;
+    m32::FF Rout;
+    float r_in2;   // 2 r_in
+    __device__ void init(double r0, double th0, double ph0, double lnP0, double R_out, float r_in)
+    {
+        r = m32::ff_from_double(r0);
+        th = m32::ff_from_double(th0);
+        ph = m32::ff_from_double(ph0);
+        lnP = m32::ff_from_double(lnP0);
+        s.hi = 0.0f; s.lo = 0.0f;
+        Rout = m32::ff_from_double(R_out);
+        r_in2 = 2.0f * r_in;
+    }
+    __device__ float fr() const { return r.hi; }
+    __device__ float fth() const { return th.hi; }
+    __device__ float fph() const { return ph.hi; }
+    __device__ float flnP() const { return lnP.hi; }
+    __device__ void add(float dr, float dth, float dph, float dlnP, float dt)
+    {
+        m32::ff_add(r, dr);
+        m32::ff_add(th, dth);
+        m32::ff_add(ph, dph);
+        m32::ff_add(lnP, dlnP);
+        m32::ff_add(s, dt);
+    }
+    // reflect at r_in, fold theta at the poles, wrap phi; all rare branches
+    __device__ void boundaries(float r_in)
+    {
+        if (r.hi < r_in) {           // r <- 2 r_in - r
+            r.hi = -r.hi; r.lo = -r.lo;
+            m32::ff_add(r, r_in2);
+        }
+        if (th.hi < 0.0f || th.hi > m32::kPiF) fold_theta();
+        if (ph.hi < 0.0f || ph.hi >= m32::kTwoPiF) wrap_phi();
+    }
+    __device__ void fold_theta()
+    {
+        // t = th mod 2 pi in [0, 2pi); if t > pi: th = 2pi - t, ph += pi
+        const double t0 = m32::ff_to_double(th);
+        double t = t0 - kTwoPi * floor(t0 / kTwoPi);
+        if (t > kPi) {
+            t = kTwoPi - t;
+            const double p = m32::ff_to_double(ph) + kPi;
+            ph = m32::ff_from_double(p);
+        }
+        th = m32::ff_from_double(t);
+    }
+    __device__ void wrap_phi()
+    {
+        const double p0 = m32::ff_to_double(ph);
+        ph = m32::ff_from_double(p0 - kTwoPi * floor(p0 / kTwoPi));
+    }
+    __device__ bool exited() const { return m32::ff_ge(r, Rout); }
+    __device__ bool finite() const { return isfinite(r.hi + th.hi + ph.hi + lnP.hi + s.hi); }
+    __device__ void write(const ExitPtrs &out, uint64_t g) const
+    {
+        out.r[g] = m32::ff_to_double(r);
+        out.th[g] = m32::ff_to_double(th);
+        out.ph[g] = m32::ff_to_double(ph);
+        out.lnP[g] = m32::ff_to_double(lnP);
+        out.s[g] = m32::ff_to_double(s);
+    }
+};
+
+// FP64 accumulation of FP32 increments
+template <>
+struct Acc<COSMICA_PREC_MIXED_F64ACC> {
+    double r, th, ph, lnP, s, Rout, r_in;
+    __device__ void init(double r0, double th0, double ph0, double lnP0, double R_out, float r_in_f)
+    {
+        r = r0; th = th0; ph = ph0; lnP = lnP0; s = 0.0; Rout = R_out; r_in = (double)r_in_f;
+    }
+    __device__ float fr() const { return (float)r; }
+    __device__ float fth() const { return (float)th; }
+    __device__ float fph() const { return (float)ph; }
+    __device__ float flnP() const { return (float)lnP; }
+    __device__ void add(float dr, float dth, float dph, float dlnP, float dt)
+    {
+        r += (double)dr; th += (double)dth; ph += (double)dph; lnP += (double)dlnP; s += (double)dt;
+    }
+    __device__ void boundaries(float)
+    {
+        if (r < r_in) r = 2.0 * r_in - r;
+        if (th < 0.0 || th > kPi) {
+            double t = th - kTwoPi * floor(th / kTwoPi);
+            if (t > kPi) { t = kTwoPi - t; ph += kPi; }
+            th = t;
+        }
+        if (ph < 0.0 || ph >= kTwoPi) ph = ph - kTwoPi * floor(ph / kTwoPi);
+    }
+    __device__ bool exited() const { return r >= Rout; }
+    __device__ bool finite() const { return isfinite(r + th + ph + lnP + s); }
+    __device__ void write(const ExitPtrs &out, uint64_t g) const
+    {
+        out.r[g] = r; out.th[g] = th; out.ph[g] = ph; out.lnP[g] = lnP; out.s[g] = s;
+    }
+};
+
+template <int ACC>
+__device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t g, Lane &L, Acc<ACC> &x)
+{
+    const uint32_t it = find_item(a.prefix, a.n_items, g);
+    const DevItem item = a.items[it];
+    const DevParams &p = a.prm[item.param_idx];
+    const DevSpecies &sp = a.spc[item.species_idx];
+    L.q = &p.f;
+    L.M2 = sp.aoz_m0_sq;
+    L.sq = sp.sgnq;
+    L.pid = item.first_pid + (g - a.prefix[it]);
+    L.seed = item.seed;
+    L.g = g;
+    L.item = it;
+    L.k = 0;
+    L.max_steps = (uint32_t)p.max_steps;
+    const double T = item.T;
+    const double P0 = sp.A / fabs(sp.Z) * sqrt(T * (T + 2.0 * sp.m0));
+    x.init(p.r0, p.th0, p.ph0, log(P0), p.R_out, p.f.r_in);
+}
+
+template <int ACC>
+__global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    Lane L;
+    Acc<ACC> x;
+    bool active = false, drained = false;
+    unsigned long long my_steps = 0;
+
+    while (true) {
+        // refill: lanes without a particle take consecutive queue entries
+        const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
+        if (need) {
+            unsigned long long base = 0;
+            const unsigned leader = __ffs(need) - 1;
+            if (lane == leader) base = atomicAdd(a.cursor, (unsigned long long)__popc(need));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (need & (1u << lane)) {
+                const uint64_t g = base + __popc(need & ((1u << lane) - 1u));
+                if (g < a.n_total) {
+                    start_particle<ACC>(a, g, L, x);
+                    active = true;
+                } else {
+                    drained = true;
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, active)) break;
+        if (!active) continue;
+
+        // one Euler-Maruyama step (Eq. 3, Eq. 6)
+        float z0, z1, z2;
+        m32::normals(L.seed, L.pid, L.k, z0, z1, z2);
+        m32::Drift c;
+        const F32Params &q = *L.q;
+        const float r = x.fr();
+        m32::eval(q, L.M2, L.sq, r, x.fth(), x.fph(), x.flnP(), c);
+        const float sdt = sqrtf(c.dt);
+        const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
+        const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);
+        const float dph = fmaf(c.dph_drift, c.dt, fmaf(c.l20, z0, c.l22 * z2) * sdt * c.inv_rs);
+        x.add(dr, dth, dph, c.dlnP * c.dt, c.dt);
+        x.boundaries(q.r_in);
+        L.k += 1u;
+
+        int status = COSMICA_PATH_RUNNING;
+        if (!x.finite()) status = COSMICA_PATH_NONFINITE;
+        else if (x.exited()) status = COSMICA_PATH_EXIT;
+        else if (L.k >= L.max_steps) status = COSMICA_PATH_STEP_LIMIT;
+        if (status != COSMICA_PATH_RUNNING) {
+            x.write(a.out, L.g);
+            a.out.steps[L.g] = L.k;
+            a.out.status[L.g] = (uint8_t)status;
+            a.out.item[L.g] = L.item;
+            my_steps += L.k;
+            active = false;
+        }
+    }
+    if (a.steps_total) {
+        for (int o = 16; o > 0; o >>= 1) my_steps += __shfl_down_sync(0xffffffffu, my_steps, o);
+        if (lane == 0 && my_steps) atomicAdd(a.steps_total, my_steps);
+    }
+}
+
+// debug: mixed coefficients at given states (FP64 in, FP64 out)
+__global__ void k_debug_eval32(const DevParams *__restrict__ prm, const DevSpecies *__restrict__ spc,
+                               uint32_t n, const double *__restrict__ st, double *__restrict__ out)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float dbg[kDebugEvalN];
+    m32::Drift c;
+    m32::eval(prm[0].f, spc[0].aoz_m0_sq, spc[0].sgnq, (float)st[4 * i], (float)st[4 * i + 1],
+              (float)st[4 * i + 2], (float)st[4 * i + 3], c, dbg);
+    for (int j = 0; j < kDebugEvalN; ++j) out[(size_t)i * kDebugEvalN + j] = dbg[j];
+}
+
+}  // namespace
+
+int mixed_max_blocks_per_sm(int acc, unsigned block)
+{
+    int nb = 0;
+    if (acc == COSMICA_PREC_MIXED_F64ACC)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<COSMICA_PREC_MIXED_F64ACC>,
+                                                      (int)block, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<COSMICA_PREC_MIXED>, (int)block, 0);
+    return nb;
+}
+
+cudaError_t launch_propagate_mixed(const LaunchArgs &a, int acc, PersistentShape shape, cudaStream_t s)
+{
+    if (a.n_total == 0) return cudaSuccess;
+    if (acc == COSMICA_PREC_MIXED_F64ACC)
+        k_propagate_mixed<COSMICA_PREC_MIXED_F64ACC><<<shape.grid, shape.block, 0, s>>>(a);
+    else
+        k_propagate_mixed<COSMICA_PREC_MIXED><<<shape.grid, shape.block, 0, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_eval32(const DevParams *prm, const DevSpecies *spc, uint32_t n, const double *st,
+                                double *out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_debug_eval32<<<(n + 127) / 128, 128, 0, s>>>(prm, spc, n, st, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace cosmica

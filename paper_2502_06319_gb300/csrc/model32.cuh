@@ -1,0 +1,250 @@
+// model32.cuh -- the mixed-precision step.
+//
+// Coefficients, the tensor square root and the normals are evaluated in FP32
+// with the SFU (MUFU) approximations of exp2/log2/sin/cos/rsqrt/rcp; the
+// state r, theta, phi, lnP and s is accumulated either as float-float pairs
+// (compensated FP32: TwoSum of each increment, error carried in a low word
+// and renormalised) or in FP64.  The outer-boundary test is exact in both:
+// a float-float value is compared lexicographically against the float-float
+// split of R_out, which equals comparing the exact sum with R_out.
+//
+// The model is the same reading as the FP64 step; the algebra is rearranged
+// for FP32 (closed forms instead of cancelling differences):
+//   (1 + tanh x)/2 = 1/(1 + e^-2x),   1 - tanh^2 x = 4 s (1 - s) with s = that logistic,
+//   L_rr = sqrt(2 K_rr), L_phr = 2 K_rph / L_rr, L_phph = K_par sqrt(2 er / K_rr)
+//   (det of the (r,ph) block is er K_par^2 because cos^2 + sin^2 = 1).
+#pragma once
+#include "common.cuh"
+#include "philox.cuh"
+
+namespace cosmica {
+namespace m32 {
+
+constexpr float kHalfPiF = 1.57079632679489662f;
+constexpr float kPiF = 3.14159265358979324f;
+constexpr float kTwoPiF = 6.28318530717958648f;
+constexpr float kInvTwoPiF = 0.159154943091895336f;
+constexpr float kSqrt2F = 1.41421356237309505f;
+
+// 1/(1 + e^{-2x}) = (1 + tanh x) / 2, safe for any finite x
+__device__ __forceinline__ float half_one_plus_tanh(float x)
+{
+    return __fdividef(1.0f, 1.0f + __expf(-2.0f * x));
+}
+
+struct Drift {
+    float Ar_tot;      // radial drift of the SDE, A^r - V - v_d,r   [AU/day]
+    float dth_drift;   // d theta / ds                                [1/day]
+    float dph_drift;   // d phi / ds                                  [1/day]
+    float l00, l11, l20, l22;
+    float inv_r, inv_rs;
+    float dlnP, dt;
+};
+
+// Coefficients at (r, th, ph, lnP).  q: FP32 constants of the heliosphere.
+// M2 = (A/|Z| m0)^2, sq = sign of the charge.
+__device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, float r, float th, float ph,
+                                     float lnP, Drift &o, float *dbg = nullptr)
+{
+    const float P = __expf(lnP);
+    const float beta = P * rsqrtf(fmaf(P, P, M2));
+    float sn, cs;
+    __sincosf(th, &sn, &cs);
+    const float inv_sn = __fdividef(1.0f, sn);
+    const float cot = cs * inv_sn;
+    const float inv_r = __fdividef(1.0f, r);
+
+    // wind V(th) and dV/dth
+    const float lat = kHalfPiF - th;
+    const float sw = half_one_plus_tanh((fabsf(lat) - q.lat_f) * q.inv_dlat);
+    const float V = fmaf(q.dV, sw, q.Vs);
+    const float sgn_lat = (lat > 0.0f) ? -1.0f : ((lat < 0.0f) ? 1.0f : 0.0f);   // d|lat|/dth
+    const float dV = q.dV * 2.0f * sw * (1.0f - sw) * q.inv_dlat * sgn_lat;
+    const float inv_V = __fdividef(1.0f, V);
+
+    // Parker spiral
+    const float Gam = q.Omega * r * sn * inv_V;
+    const float G2 = Gam * Gam;
+    const float iq = __fdividef(1.0f, 1.0f + G2);
+    const float dGam_dth = Gam * (cot - dV * inv_V);
+
+    // termination shock factor
+    const float st = half_one_plus_tanh((r - q.R_ts) * q.inv_dts);
+    const float g = fmaf(-q.ts_drop, st, 1.0f);
+    const float dg = -q.ts_drop * 2.0f * st * (1.0f - st) * q.inv_dts;
+
+    // diffusion tensor in (r, th, ph); K_rth = K_thph = 0
+    const float Kb = q.K0 * beta * P;
+    const float Kpar = Kb * g;
+    const float dKpar = Kb * dg;
+    const float c2s = fmaf(q.er, G2 * iq, iq);            // cos^2 + er sin^2
+    const float iq2 = iq * iq;
+    const float dc2_dr = -2.0f * G2 * iq2 * inv_r;         // d cos^2 psi / dr
+    const float sc = Gam * iq;
+    const float dsc_dr = Gam * (1.0f - G2) * iq2 * inv_r;
+    const float Krr = Kpar * c2s;
+    const float erm1 = q.er - 1.0f;
+    const float Krp = erm1 * Kpar * sc;
+    const float Ktt = q.et * Kpar;
+    const float dKrr = fmaf(dKpar, c2s, -Kpar * erm1 * dc2_dr);
+    const float dKrp = erm1 * fmaf(dKpar, sc, Kpar * dsc_dr);
+
+    // Ito drift (1/sqrt g) d_j (sqrt g K^ij)
+    const float Ar = fmaf(2.0f * Krr, inv_r, dKrr);
+    const float Ath = Ktt * cot * inv_r * inv_r;
+    const float inv_rs = inv_r * inv_sn;
+    const float Aph = fmaf(Krp, inv_r, dKrp) * inv_rs;
+
+    // Cholesky factor of 2K
+    const float rK = rsqrtf(Krr);
+    o.l00 = kSqrt2F * Krr * rK;
+    o.l20 = kSqrt2F * Krp * rK;
+    o.l22 = q.sqrt2er * Kpar * rK;
+    o.l11 = sqrtf(2.0f * Ktt);
+
+    // drift v_d = sgn(qA) curl(kappa_A h e_B)
+    float vd0 = 0.0f, vd1 = 0.0f, vd2 = 0.0f, delta = 0.0f, h = 1.0f;
+    if (q.drift != 0.0f) {
+        const float r2 = r * r;
+        const float F = r2 * iq;
+        const float Gf = F * Gam;
+        const float dF_dth = -2.0f * r2 * Gam * dGam_dth * iq2;
+        const float dGf_dr = r * Gam * (3.0f + G2) * iq2;
+        const float dGf_dth = r2 * dGam_dth * (1.0f - G2) * iq2;
+        float hr = 0.0f, ht = 0.0f, hp = 0.0f;
+        if (q.hcs != 0.0f) {
+            const float phs = fmaf(q.Omega * r, inv_V, ph);
+            const float dphs_dr = q.Omega * inv_V;
+            const float dphs_dth = -q.Omega * r * dV * inv_V * inv_V;
+            const float red = fmaf(-kTwoPiF, rintf(phs * kInvTwoPiF), phs);
+            float sp, cp;
+            __sincosf(red, &sp, &cp);
+            const float th_cs = kHalfPiF + atanf(q.ta * sp);
+            const float dthcs = __fdividef(q.ta * cp, fmaf(q.ta2, sp * sp, 1.0f));
+            const float sqiq = sqrtf(iq);
+            const float w_rl = q.D2 * P * r * sqiq;
+            float dd_dr = 0.0f, dd_dth = 0.0f;
+            if (w_rl > q.dcs_min) {
+                delta = w_rl;
+                const float k3 = q.D2 * P * iq * sqiq;
+                dd_dr = k3;
+                dd_dth = -k3 * r * Gam * dGam_dth;
+            } else {
+                delta = q.dcs_min;
+            }
+            const float inv_d = __fdividef(1.0f, delta);
+            const float u = (th_cs - th) * inv_d;
+            const float sh = half_one_plus_tanh(u);
+            h = 2.0f * sh - 1.0f;
+            const float sech2 = 4.0f * sh * (1.0f - sh);
+            hr = sech2 * (dthcs * dphs_dr - u * dd_dr) * inv_d;
+            ht = sech2 * (dthcs * dphs_dth - 1.0f - u * dd_dth) * inv_d;
+            hp = sech2 * dthcs * inv_d;
+        }
+        const float s = sq * q.polarity * q.CA0 * beta * P * inv_r;
+        const float Wph = -h * Gf;                       // W_ph / C_A
+        const float dWph_dth = -fmaf(ht, Gf, h * dGf_dth);
+        const float dWph_dr = -fmaf(hr, Gf, h * dGf_dr);
+        vd0 = s * fmaf(cot, Wph, dWph_dth);
+        vd1 = s * (hp * F * inv_sn - Wph - r * dWph_dr);
+        vd2 = -s * fmaf(ht, F, h * dF_dth);
+    }
+
+    const float Ar_tot = Ar - V - vd0;
+    o.Ar_tot = Ar_tot;
+    o.dth_drift = Ath - vd1 * inv_r;
+    o.dph_drift = Aph - vd2 * inv_rs;
+    o.inv_r = inv_r;
+    o.inv_rs = inv_rs;
+    o.dlnP = 0.66666666666666667f * V * inv_r;
+
+    // step length
+    float dt;
+    if (q.dt_fixed > 0.0f) {
+        dt = q.dt_fixed;
+    } else {
+        const float t1 = __fdividef(q.eps_adv2 * Krr, Ar_tot * Ar_tot);
+        const float t2 = __fdividef(q.eps_diff * r * r, Krr);
+        dt = fminf(q.dt_max, fminf(t1, t2));
+        if (delta > 0.0f) {
+            const float rd = r * delta;
+            dt = fminf(dt, __fdividef(q.eps_diff * rd * rd, Ktt));
+        }
+        dt = fmaxf(dt, q.dt_min);
+    }
+    o.dt = dt;
+    if (dbg) {
+        dbg[0] = V; dbg[1] = Gam; dbg[2] = Kpar; dbg[3] = Krr; dbg[4] = Ktt; dbg[5] = Kpar * fmaf(G2, iq, q.er * iq);
+        dbg[6] = Krp; dbg[7] = Ar; dbg[8] = Ath; dbg[9] = Aph; dbg[10] = o.l00; dbg[11] = o.l11;
+        dbg[12] = o.l20; dbg[13] = o.l22; dbg[14] = h; dbg[15] = delta;
+        dbg[16] = vd0; dbg[17] = vd1; dbg[18] = vd2; dbg[19] = o.dlnP; dbg[20] = dt;
+    }
+}
+
+// Three N(0,1) in FP32: Box-Muller on the Philox words mapped to (0,1] as
+// ((x >> 8) + 1/2) 2^-24.
+__device__ __forceinline__ void normals(uint64_t seed, uint64_t pid, uint32_t k, float &z0, float &z1,
+                                        float &z2)
+{
+    const uint4 w = philox_step_block(seed, pid, k);
+    const float sc = 5.9604644775390625e-8f;    // 2^-24
+    const float u0 = fmaf((float)(w.x >> 8), sc, 0.5f * sc);
+    const float u1 = fmaf((float)(w.y >> 8), sc, 0.5f * sc);
+    const float u2 = fmaf((float)(w.z >> 8), sc, 0.5f * sc);
+    const float u3 = fmaf((float)(w.w >> 8), sc, 0.5f * sc);
+    const float rho0 = sqrtf(-2.0f * __logf(u0));
+    const float rho2 = sqrtf(-2.0f * __logf(u2));
+    // angle 2 pi u - pi lies in (-pi, pi], where the SFU sin/cos are accurate;
+    // cos(a - pi) = -cos a, sin(a - pi) = -sin a
+    float s1, c1, s3, c3;
+    __sincosf(fmaf(u1, kTwoPiF, -kPiF), &s1, &c1);
+    __sincosf(fmaf(u3, kTwoPiF, -kPiF), &s3, &c3);
+    z0 = -rho0 * c1;
+    z1 = -rho0 * s1;
+    z2 = -rho2 * c3;
+}
+
+// ---- compensated FP32 accumulation ---------------------------------------
+struct FF {
+    float hi, lo;
+};
+
+// (hi, lo) += d: TwoSum of hi + d, error carried into lo, then renormalised
+// so that |lo| <= ulp(hi)/2.
+__device__ __forceinline__ void ff_add(FF &a, float d)
+{
+    const float s = a.hi + d;
+    const float bb = s - a.hi;
+    const float err = (a.hi - (s - bb)) + (d - bb);
+    const float lo = a.lo + err;
+    const float hi = s + lo;
+    a.lo = lo - (hi - s);
+    a.hi = hi;
+}
+
+__device__ __forceinline__ void ff_add_ff(FF &a, float bh, float bl)
+{
+    ff_add(a, bh);
+    ff_add(a, bl);
+}
+
+__device__ __forceinline__ FF ff_from_double(double x)
+{
+    FF r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+
+__device__ __forceinline__ double ff_to_double(const FF &a) { return (double)a.hi + (double)a.lo; }
+
+// exact test a >= b for normalised float-float values
+__device__ __forceinline__ bool ff_ge(const FF &a, const FF &b)
+{
+    return (a.hi > b.hi) || (a.hi == b.hi && a.lo >= b.lo);
+}
+
+__device__ __forceinline__ bool ff_lt(const FF &a, const FF &b) { return !ff_ge(a, b); }
+
+}  // namespace m32
+}  // namespace cosmica

@@ -1,0 +1,85 @@
+"""The C-ABI library builds for sm_103a, loads, exports every symbol its
+headers declare, and rejects malformed arguments on the host before any
+device work (no GPU needed for these paths)."""
+import ctypes as C
+import subprocess
+
+import pytest
+
+from paper_2502_06319_gb300 import cosmica as cz
+
+
+def test_library_exports_every_declared_symbol():
+    L = cz.lib()
+    names = cz.exported_symbols()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(L, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", cz._build.LIB], capture_output=True, text=True).stdout
+    for n in names:
+        assert f" T {n}" in out, n
+
+
+def test_params_layout_and_defaults():
+    p = cz.cosmica_params()
+    cz.lib().cosmica_params_default(C.byref(p))
+    assert p.struct_size == C.sizeof(cz.cosmica_params)
+    assert p.version == cz.ABI_VERSION
+    assert p.K0 == 11.5 and p.R_out_AU == 100.0 and p.max_steps == 100_000_000
+    assert p.precision == cz.PREC_FP64 and p.polarity == 1
+
+
+def _status(f, *a):
+    return f(*a)
+
+
+def test_invalid_arguments_are_rejected_on_the_host():
+    L = cz.lib()
+    h = C.c_void_p()
+    assert L.cosmica_model_create(None, C.byref(h)) == cz.ERR_INVALID
+    assert b"NULL" in L.cosmica_last_error()
+    p = cz.make_params({})
+    p.struct_size = 8
+    assert L.cosmica_model_create(C.byref(p), C.byref(h)) == cz.ERR_INVALID
+    assert b"struct_size" in L.cosmica_last_error()
+    p = cz.make_params({"R_out": 0.5})
+    assert L.cosmica_model_create(C.byref(p), C.byref(h)) == cz.ERR_INVALID
+    p = cz.make_params({"polarity": 0})
+    assert L.cosmica_model_create(C.byref(p), C.byref(h)) == cz.ERR_INVALID
+    p = cz.make_params({}, precision=7)
+    assert L.cosmica_model_create(C.byref(p), C.byref(h)) == cz.ERR_INVALID
+    assert h.value is None
+    # propagate / batch with NULL handles
+    assert L.cosmica_propagate(None, None, None, 0, None, 1, None, None) == cz.ERR_INVALID
+    assert L.cosmica_batch_create(None, 0, None, 0, C.byref(h)) == cz.ERR_INVALID
+    assert L.cosmica_batch_run(None, None, 0, None, None, None, None) == cz.ERR_INVALID
+    assert L.cosmica_debug_fn64(9, 0, None, None, None) == cz.ERR_INVALID
+
+
+def test_error_message_is_thread_local():
+    import threading
+    L = cz.lib()
+    h = C.c_void_p()
+    L.cosmica_model_create(None, C.byref(h))
+    seen = {}
+
+    def other():
+        seen["msg"] = L.cosmica_last_error()
+
+    t = threading.Thread(target=other)
+    t.start(); t.join()
+    assert seen["msg"] == b""
+    assert L.cosmica_last_error() != b""
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle is C compiled by gcc; the library never includes or links it."""
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    csrc = os.path.join(root, "paper_2502_06319_gb300", "csrc")
+    for f in os.listdir(csrc):
+        txt = open(os.path.join(csrc, f)).read()
+        assert "oracle" not in txt.lower(), f
+    for f in ("cosmica.py", "_build.py", "__init__.py", "workloads.py"):
+        txt = open(os.path.join(root, "paper_2502_06319_gb300", f)).read()
+        assert "import oracle" not in txt and "from oracle" not in txt, f
