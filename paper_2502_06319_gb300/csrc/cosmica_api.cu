@@ -44,6 +44,7 @@ cosmica_status fail(cosmica_status st, const char *fmt, ...)
 
 cosmica_status cuda_fail(cudaError_t e, const char *what)
 {
+    cudaGetLastError();   // a reported failure must not resurface at a later launch check
     if (e == cudaErrorMemoryAllocation)
         return fail(COSMICA_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
     return fail(COSMICA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -229,14 +230,19 @@ struct ExitStage {
     DevBuf buf;
     cosmica_status make(uint64_t n, ExitPtrs &d)
     {
-        const size_t per = 5 * sizeof(double) + 2 * sizeof(uint32_t) + 1;
-        cosmica_status st = buf.reserve(align_up(n * per + 64 * 8, 256));
+        // eight arrays, each starting on a 256-byte boundary
+        const size_t a8 = align_up(n * 8, 256), a4 = align_up(n * 4, 256), a1 = align_up(n, 256);
+        cosmica_status st = buf.reserve(5 * a8 + 2 * a4 + a1);
         if (st != COSMICA_OK) return st;
         char *p = (char *)buf.d;
-        auto take = [&](size_t bytes) { char *q = p; p += align_up(bytes, 256); return q; };
-        d.r = (double *)take(n * 8); d.th = (double *)take(n * 8); d.ph = (double *)take(n * 8);
-        d.lnP = (double *)take(n * 8); d.s = (double *)take(n * 8);
-        d.steps = (uint32_t *)take(n * 4); d.item = (uint32_t *)take(n * 4); d.status = (uint8_t *)take(n);
+        d.r = (double *)p;   p += a8;
+        d.th = (double *)p;  p += a8;
+        d.ph = (double *)p;  p += a8;
+        d.lnP = (double *)p; p += a8;
+        d.s = (double *)p;   p += a8;
+        d.steps = (uint32_t *)p; p += a4;
+        d.item = (uint32_t *)p;  p += a4;
+        d.status = (uint8_t *)p;
         return COSMICA_OK;
     }
     static cosmica_status copy_back(const ExitPtrs &d, const cosmica_exit_states *o, cudaStream_t s)

@@ -27,6 +27,7 @@ cudaError_t launch_debug_curand_philox(uint32_t n, uint64_t seed, const unsigned
                                        const unsigned long long *offset, uint32_t *out, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
+    cudaGetLastError();
     k_debug_curand_philox<<<(n + 127) / 128, 128, 0, s>>>(n, seed, subseq, offset, out);
     note_launch();
     return cudaGetLastError();

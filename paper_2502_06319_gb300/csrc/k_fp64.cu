@@ -146,6 +146,7 @@ static inline unsigned grid_for(uint64_t n, unsigned block) { return (unsigned)(
 cudaError_t launch_derive(DevParams *prm, uint32_t n, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
+    cudaGetLastError();
     k_derive<<<grid_for(n, 64), 64, 0, s>>>(prm, n);
     note_launch();
     return cudaGetLastError();
@@ -154,6 +155,7 @@ cudaError_t launch_derive(DevParams *prm, uint32_t n, cudaStream_t s)
 cudaError_t launch_propagate_fp64(const LaunchArgs &a, cudaStream_t s)
 {
     if (a.n_total == 0) return cudaSuccess;
+    cudaGetLastError();
     k_propagate_fp64<<<grid_for(a.n_total, 128), 128, 0, s>>>(a.prm, a.spc, a.items, a.prefix, a.n_items,
                                                              a.n_total, a.out, a.steps_total);
     note_launch();
@@ -164,6 +166,7 @@ cudaError_t launch_debug_eval64(const DevParams *prm, const DevSpecies *spc, uin
                                 double *out, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
+    cudaGetLastError();
     k_debug_eval64<<<grid_for(n, 128), 128, 0, s>>>(prm, spc, n, st, out);
     note_launch();
     return cudaGetLastError();
@@ -172,6 +175,7 @@ cudaError_t launch_debug_eval64(const DevParams *prm, const DevSpecies *spc, uin
 cudaError_t launch_debug_fn64(int which, uint32_t n, const double *x, double *y, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
+    cudaGetLastError();
     k_debug_fn64<<<grid_for(n, 256), 256, 0, s>>>(which, n, x, y);
     note_launch();
     return cudaGetLastError();
@@ -181,6 +185,7 @@ cudaError_t launch_debug_normals64(uint64_t seed, uint64_t pid0, uint32_t n, uin
                                    cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
+    cudaGetLastError();
     k_debug_normals64<<<grid_for(n, 256), 256, 0, s>>>(seed, pid0, n, step, z);
     note_launch();
     return cudaGetLastError();
@@ -190,6 +195,7 @@ cudaError_t launch_debug_philox(uint32_t n, const uint32_t *ctr, uint32_t k0, ui
                                 cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
+    cudaGetLastError();
     k_debug_philox<<<grid_for(n, 256), 256, 0, s>>>(n, ctr, k0, k1, out);
     note_launch();
     return cudaGetLastError();

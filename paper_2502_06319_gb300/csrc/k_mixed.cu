@@ -246,6 +246,7 @@ int mixed_max_blocks_per_sm(int acc, unsigned block)
 cudaError_t launch_propagate_mixed(const LaunchArgs &a, int acc, PersistentShape shape, cudaStream_t s)
 {
     if (a.n_total == 0) return cudaSuccess;
+    cudaGetLastError();
     if (acc == COSMICA_PREC_MIXED_F64ACC)
         k_propagate_mixed<COSMICA_PREC_MIXED_F64ACC><<<shape.grid, shape.block, 0, s>>>(a);
     else
@@ -258,6 +259,7 @@ cudaError_t launch_debug_eval32(const DevParams *prm, const DevSpecies *spc, uin
                                 double *out, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
+    cudaGetLastError();
     k_debug_eval32<<<(n + 127) / 128, 128, 0, s>>>(prm, spc, n, st, out);
     note_launch();
     return cudaGetLastError();

@@ -137,6 +137,7 @@ cudaError_t launch_histogram(const ExitPtrs &ex, uint64_t n, uint32_t n_items, u
                              double dx, unsigned long long *hist, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
+    cudaGetLastError();
     k_histogram<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ex, n, n_items, nbins, x_lo, dx, hist);
     note_launch();
     return cudaGetLastError();
@@ -147,6 +148,7 @@ cudaError_t launch_spectrum(const unsigned long long *hist, uint32_t n_items, ui
                             const double *lis_lnJ, uint32_t lis_n, double *J, double *sigma, cudaStream_t s)
 {
     if (n_items == 0) return cudaSuccess;
+    cudaGetLastError();
     k_spectrum<<<n_items, kSpecThreads, 0, s>>>(hist, nbins, x_lo, dx, items, lis_kind, lis_lnT, lis_lnJ,
                                                 lis_n, J, sigma);
     note_launch();

@@ -152,6 +152,8 @@ def test_fp32_coefficients_close(orc, model):
         scale_v = abs(ref["V"]) + abs(ref["vdr"]) + abs(ref["vdth"]) + abs(ref["vdph"])
         for j, name in enumerate(cz.DEBUG_EVAL_NAMES):
             a, b = got[i, j], ref[_ORACLE_NAMES[name]]
+            if name in ("h", "delta_cs") and not MODELS[model]["drift_on"]:
+                continue   # the sheet only enters through the drift
             if name in ("vdr", "vdth", "vdph"):
                 tol = 2e-3 * scale_v + 1e-6
             elif name in ("Ar", "Ath", "Aph"):
