@@ -54,9 +54,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--c4-requests", type=int, default=24, help="requests per serving run")
     ap.add_argument("--c3-scale", type=float, default=1.0, help="scale of config-3 particle counts")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_f64acc", "fp64"])
+    ap.add_argument("--scale", type=float, default=1.0, help="scale of config-1/2 particles per energy")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shape instead of the autotuner")
+    ap.add_argument("--precision", default=None, choices=["mixed", "mixed_f64acc", "fp64"],
+                    help="default: compensated FP32 for configs 1-2, FP64 accumulation for configs 3-4")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--cpu-sample", type=int, default=0, help="particles per energy in the oracle sample")
@@ -65,10 +69,14 @@ def parse():
 
 def workload(args):
     """Jobs (one per spectrum) of the chosen configuration."""
+    if args.workload == "c4":
+        return [r.job for r in W.config4(n_requests=args.c4_requests)], "config4 request sample"
     if args.workload == "c1":
-        return [W.config1()], "config1: full model FP64-spec, proton, 10 energies x 5000"
+        n = max(1, int(round(5000 * args.scale)))
+        return [W.config1(n)], f"config1: full model, proton, 10 energies x {n}"
     if args.workload == "c2":
-        return [W.config2()], "config2: full model, proton, 30 energies x 20000"
+        n = max(1, int(round(20000 * args.scale)))
+        return [W.config2(n)], f"config2: full model, proton, 30 energies x {n}"
     jobs = W.config3(scale=args.c3_scale)
     return jobs, f"config3: 64 heliospheres x 3 species x 30 energies, counts 1e3-5e4 (scale {args.c3_scale})"
 
@@ -182,8 +190,64 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_bench(args, cz, torch):
+    """Config 4: the continuous-batching server under a Poisson request stream."""
+    import math as _m
+    reqs = W.config4(n_requests=4 * args.c4_requests)
+    prec = cz.PREC_MIXED if args.precision == "mixed" else cz.PREC_MIXED_F64ACC
+    bins = cz.make_bins(0.1, 1000.0, 512)
+
+    def make(r):
+        j = r.job
+        return cz.Request(cz.make_params(j.params, prec), cz.make_species(j.species), j.T_in, j.n_per_energy,
+                          j.seed, bins)
+
+    def run(batch, arrivals):
+        srv = cz.cosmica_server_create(48 << 30, prec, budget_steps=4096)
+        t0 = time.perf_counter()
+        tickets = []
+        for (r, ta) in zip(batch, arrivals):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append((cz.cosmica_server_submit(srv, make(r)), r))
+        lat, steps = [], 0
+        for t, r in tickets:
+            res = cz.Result(len(r.job.T_in), 512)
+            cz.cosmica_server_wait(srv, t, res, timeout_ms=3_600_000)
+            lat.append(res.latency)
+            steps += res.steps
+        wall = time.perf_counter() - t0
+        st = cz.cosmica_server_stats_get(srv)
+        cz.cosmica_server_destroy(srv)
+        return {"wall_s": wall, "steps": steps, "lat": lat, "quanta": st["quanta"], "busy_s": st["busy_seconds"]}
+
+    M = args.c4_requests
+    nE = np.mean([len(r.job.T_in) for r in reqs[:M]])
+    # per request: parameters + species + energies/counts + queue slices up; J, sigma, histogram down
+    h2d = int(232 + 16 + nE * (8 + 4 + 48 + 8))
+    d2h = int(nE * (16 + (512 + 3) * 8))
+    # warm-up (module load, first-launch costs)
+    run(reqs[:2], [0.0, 0.0])
+    cap = run(reqs[:M], [0.0] * M)                     # all queued at once: capacity
+    cap_rps = M / cap["wall_s"]
+    out = {"h2d_bytes_per_request": h2d, "d2h_bytes_per_request": d2h,
+           "capacity": {"requests_per_s": cap_rps, "steps_per_s": cap["steps"] / cap["wall_s"],
+                        "quanta": cap["quanta"]}}
+    rng = np.random.default_rng(20250211)
+    for name, rate in (("load_0.5", 0.5 * cap_rps), ("load_0.8", 0.8 * cap_rps), ("offered_200", 200.0)):
+        arr = np.cumsum(rng.exponential(1.0 / rate, M))
+        rr = run(reqs[M:2 * M] if name != "offered_200" else reqs[2 * M:3 * M], arr)
+        lat = np.sort(rr["lat"])
+        out[name] = {"rate_rps": rate, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                     "spectra_per_s": M / rr["wall_s"], "steps_per_s": rr["steps"] / rr["wall_s"]}
+    return out, cap
+
+
 def main():
     args = parse()
+    if args.precision is None:
+        args.precision = "mixed" if args.workload in ("c1", "c2") else "mixed_f64acc"
     if args.impl == "reference":
         return run_reference(args)
     import torch
@@ -200,6 +264,27 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
+    if args.workload == "c4":
+        launches0 = cz.cosmica_launch_count()
+        clocks = Clocks(local)
+        clocks.start()
+        res, cap = serve_bench(args, cz, torch)
+        clk = clocks.stop()
+        v = res["capacity"]["steps_per_s"]
+        line = {"metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world, "steps": args.c4_requests,
+                "warmup": 2, "ms_per_step": 1e3 / res["capacity"]["requests_per_s"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc" if args.precision != "mixed" else "f32+ff",
+                "data": "synthetic", "config": {"workload": "config4: Poisson request stream (seed 20250211), "
+                                                "1 heliosphere x 1 species x 4-30 energies x 2e3-1e5 particles",
+                                                "server": "continuous batching, 4096 steps/lane/quantum, 48 GB budget",
+                                                "step": "one request (= one spectrum)"},
+                "spectra_per_s": res["capacity"]["requests_per_s"], "serving": res,
+                "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": res["h2d_bytes_per_request"],
+                        "d2h_bytes_per_step": res["d2h_bytes_per_request"]},
+                "gpu_launches": cz.cosmica_launch_count() - launches0, "clocks": clk}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     jobs, desc = workload(args)
     prec = {"mixed": cz.PREC_MIXED, "mixed_f64acc": cz.PREC_MIXED_F64ACC, "fp64": cz.PREC_FP64}[args.precision]
     params, species, items = items_of(jobs, rank)
@@ -216,7 +301,10 @@ def main():
     arr = cz.make_items(items)
     nI = len(items)
     batch = make_batch(prec)
-    tune, tune_rate = cz.cosmica_autotune(batch, arr, nI)
+    if args.no_autotune:
+        tune = cz.cosmica_tuning(128, 0, 1, 0)
+    else:
+        tune, tune_rate = cz.cosmica_autotune(batch, arr, nI)
     tune.use_graph = 1
     out = cz.ExitBuffers(n_total)
     J = torch.empty(nI, dtype=torch.float64, device="cuda")

@@ -268,6 +268,73 @@ cosmica_status cosmica_batch_spectrum(cosmica_batch *batch, const cosmica_work_i
 cosmica_status cosmica_autotune(cosmica_batch *batch, const cosmica_work_item *items,
                                 uint32_t n_items, cosmica_tuning *best, double *best_rate);
 
+/* ---------------- continuous-batching server (spectrum requests) ---------------- */
+
+/* One spectrum request: one heliosphere, one species, n_energies energies.
+ * All pointers are host memory, read only during cosmica_server_submit. */
+typedef struct {
+    cosmica_params params;        /* precision must equal the server's       */
+    cosmica_species species;
+    const double *T_GeVn;         /* [n_energies]                             */
+    const uint32_t *n_per_energy; /* [n_energies]                             */
+    uint32_t n_energies;
+    uint64_t seed;                /* particle e,i has pid = sum_{e'<e} n_e' + i */
+    cosmica_bins bins;
+} cosmica_request;
+
+/* Result of a finished request.  The caller provides the host arrays:
+ * J, sigma [n_energies] and hist [n_energies * (nbins + 3)] (may be NULL). */
+typedef struct {
+    double *J;
+    double *sigma;
+    uint64_t *hist;
+    uint64_t steps;               /* SDE steps of the request's paths             */
+    double t_submit, t_admit, t_done;   /* seconds on the server's monotonic clock */
+} cosmica_result;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, rejected;
+    uint64_t quanta;              /* persistent launches so far                  */
+    uint64_t steps;               /* SDE steps of completed requests             */
+    uint64_t in_flight_particles; /* admitted, not yet exited                    */
+    uint64_t arena_capacity, arena_used;   /* exit-state slots (particles)     */
+    double busy_seconds;          /* wall time with work on the device           */
+} cosmica_server_stats;
+
+typedef struct cosmica_server cosmica_server;
+
+/*
+ * Create a server on the current device.  mem_budget_bytes bounds the device
+ * memory the server may hold for admitted requests (exit states 49 B per
+ * particle, histograms, per-slot parameters) plus its fixed suspend/resume
+ * buffers; it is allocated once here.  precision: COSMICA_PREC_MIXED or
+ * COSMICA_PREC_MIXED_F64ACC.  budget_steps: steps per lane per quantum (0 = 4096).
+ * A scheduler thread runs quanta on the server's own stream: between quanta
+ * it admits waiting requests (first come, first served) while their memory
+ * fits and retires finished ones (histogram + spectrum, copied to the host);
+ * in-flight particles stay resident on the device, suspended exactly.
+ * Errors: INVALID, OOM, CUDA.
+ */
+cosmica_status cosmica_server_create(size_t mem_budget_bytes, int32_t precision, uint32_t budget_steps,
+                                     cosmica_server **out);
+
+/* Queue a request (non-blocking).  *ticket identifies it.  INVALID if the
+ * request can never fit the memory budget or its fields are invalid. */
+cosmica_status cosmica_server_submit(cosmica_server *srv, const cosmica_request *req, uint64_t *ticket);
+
+/* Non-blocking: OK and *res filled (the ticket is then released) if the
+ * request is finished; BUSY if not yet; INVALID for an unknown ticket. */
+cosmica_status cosmica_server_poll(cosmica_server *srv, uint64_t ticket, cosmica_result *res);
+
+/* As poll, waiting at most timeout_ms; TIMEOUT if still not finished. */
+cosmica_status cosmica_server_wait(cosmica_server *srv, uint64_t ticket, uint32_t timeout_ms,
+                                   cosmica_result *res);
+
+cosmica_status cosmica_server_stats_get(cosmica_server *srv, cosmica_server_stats *st);
+
+/* Stop the scheduler (finishing the current quantum), free everything. */
+void cosmica_server_destroy(cosmica_server *srv);
+
 /* Thread-local text of the last error of this thread ("" if none). */
 const char *cosmica_last_error(void);
 

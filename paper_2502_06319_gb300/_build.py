@@ -3,9 +3,9 @@
 Each translation unit gets the floating-point flags its arithmetic needs:
   * k_fp64.cu, k_spectrum.cu: -fmad=false -- FP64 expressions evaluated exactly
     as written (no FMA contraction), so the FP64 path is reproducible bit for bit;
-  * k_mixed.cu: --use_fast_math -- the mixed path deliberately uses the SFU
-    approximations and FMA;
-  * cosmica_api.cu, k_debug_curand.cu: defaults.
+  * k_mixed.cu, k_serve.cu: --use_fast_math -- the mixed path deliberately
+    uses the SFU approximations and FMA;
+  * cosmica_api.cu, server.cu, k_debug_curand.cu: defaults.
 Objects are compiled in parallel and linked into one shared library next to
 this file.
 """
@@ -31,6 +31,8 @@ UNITS = {
     "k_fp64.cu": ["-fmad=false"],
     "k_spectrum.cu": ["-fmad=false"],
     "k_mixed.cu": ["--use_fast_math"],
+    "k_serve.cu": ["--use_fast_math"],
+    "server.cu": [],
     "k_debug_curand.cu": [],
 }
 

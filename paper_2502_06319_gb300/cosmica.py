@@ -70,6 +70,24 @@ class cosmica_tuning(C.Structure):
                 ("use_graph", C.c_uint32)]
 
 
+class cosmica_request(C.Structure):
+    _fields_ = [("params", cosmica_params), ("species", cosmica_species), ("T_GeVn", C.c_void_p),
+                ("n_per_energy", C.c_void_p), ("n_energies", C.c_uint32), ("seed", C.c_uint64),
+                ("bins", cosmica_bins)]
+
+
+class cosmica_result(C.Structure):
+    _fields_ = [("J", C.c_void_p), ("sigma", C.c_void_p), ("hist", C.c_void_p), ("steps", C.c_uint64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+class cosmica_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
+                ("rejected", C.c_uint64), ("quanta", C.c_uint64), ("steps", C.c_uint64),
+                ("in_flight_particles", C.c_uint64), ("arena_capacity", C.c_uint64), ("arena_used", C.c_uint64),
+                ("busy_seconds", C.c_double)]
+
+
 class CosmicaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"cosmica status {status}: {msg}")
@@ -107,6 +125,15 @@ def lib():
                                                  C.POINTER(cosmica_bins), P, P, P, P]
             L.cosmica_autotune.argtypes = [P, C.POINTER(cosmica_work_item), C.c_uint32, C.POINTER(cosmica_tuning),
                                            C.POINTER(C.c_double)]
+            L.cosmica_server_create.argtypes = [C.c_size_t, C.c_int32, C.c_uint32, C.POINTER(P)]
+            L.cosmica_server_submit.argtypes = [P, C.POINTER(cosmica_request), C.POINTER(C.c_uint64)]
+            L.cosmica_server_poll.argtypes = [P, C.c_uint64, C.POINTER(cosmica_result)]
+            L.cosmica_server_wait.argtypes = [P, C.c_uint64, C.c_uint32, C.POINTER(cosmica_result)]
+            L.cosmica_server_stats_get.argtypes = [P, C.POINTER(cosmica_server_stats)]
+            L.cosmica_server_destroy.argtypes = [P]
+            for name in ("cosmica_server_create", "cosmica_server_submit", "cosmica_server_poll",
+                         "cosmica_server_wait", "cosmica_server_stats_get"):
+                getattr(L, name).restype = C.c_int
             L.cosmica_last_error.restype = C.c_char_p
             L.cosmica_launch_count.restype = C.c_uint64
             L.cosmica_debug_philox.argtypes = [C.c_uint32, P, C.c_uint32, C.c_uint32, P, P]
@@ -304,6 +331,71 @@ def cosmica_last_error() -> str:
 
 def cosmica_launch_count() -> int:
     return int(lib().cosmica_launch_count())
+
+
+# -------------------------------------------------------------- server API --
+def cosmica_server_create(mem_budget: int, precision: int = PREC_MIXED, budget_steps: int = 0) -> int:
+    h = P()
+    _check(lib().cosmica_server_create(int(mem_budget), int(precision), int(budget_steps), C.byref(h)))
+    return h.value
+
+
+def cosmica_server_destroy(h: int) -> None:
+    lib().cosmica_server_destroy(h)
+
+
+class Request:
+    """A spectrum request with its host arrays kept alive."""
+
+    def __init__(self, params: cosmica_params, species: cosmica_species, T_in, n_per_energy, seed: int,
+                 bins: cosmica_bins):
+        self.T = (C.c_double * len(T_in))(*[float(t) for t in T_in])
+        self.N = (C.c_uint32 * len(T_in))(*[int(x) for x in n_per_energy])
+        self.c = cosmica_request(params, species, C.cast(self.T, C.c_void_p), C.cast(self.N, C.c_void_p),
+                                 len(T_in), int(seed), bins)
+        self.n_energies = len(T_in)
+        self.nbins = bins.nbins
+
+
+def cosmica_server_submit(srv: int, req: Request) -> int:
+    t = C.c_uint64()
+    _check(lib().cosmica_server_submit(srv, C.byref(req.c), C.byref(t)))
+    return t.value
+
+
+class Result:
+    def __init__(self, n_energies: int, nbins: int):
+        import numpy as np
+        self.J = np.zeros(n_energies)
+        self.sigma = np.zeros(n_energies)
+        self.hist = np.zeros((n_energies, nbins + 3), dtype=np.uint64)
+        self.c = cosmica_result(self.J.ctypes.data, self.sigma.ctypes.data, self.hist.ctypes.data, 0, 0, 0, 0)
+
+    @property
+    def steps(self):
+        return self.c.steps
+
+    @property
+    def latency(self):
+        return self.c.t_done - self.c.t_submit
+
+
+def cosmica_server_poll(srv: int, ticket: int, res: Result) -> bool:
+    st = lib().cosmica_server_poll(srv, ticket, C.byref(res.c))
+    if st == ERR_BUSY:
+        return False
+    _check(st)
+    return True
+
+
+def cosmica_server_wait(srv: int, ticket: int, res: Result, timeout_ms: int = 600_000) -> None:
+    _check(lib().cosmica_server_wait(srv, ticket, int(timeout_ms), C.byref(res.c)))
+
+
+def cosmica_server_stats_get(srv: int) -> dict:
+    st = cosmica_server_stats()
+    _check(lib().cosmica_server_stats_get(srv, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in cosmica_server_stats._fields_}
 
 
 # --------------------------------------------------------------- debug API --

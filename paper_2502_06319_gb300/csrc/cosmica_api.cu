@@ -24,12 +24,14 @@
 #include "common.cuh"
 #include "cosmica.h"
 #include "cosmica_debug.h"
+#include "host_util.h"
 #include "internal.h"
 
 using namespace cosmica;
 
 // ------------------------------------------------------------------ errors --
-namespace {
+namespace cosmica {
+namespace host {
 thread_local char g_err[512] = "";
 std::atomic<unsigned long long> g_launches{0};
 
@@ -50,83 +52,6 @@ cosmica_status cuda_fail(cudaError_t e, const char *what)
     return fail(COSMICA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CK(call, what)                                   \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
-
-// Grow-only device buffer.  cudaFree synchronises the device, so a buffer is
-// never released while a kernel that uses it is in flight.
-struct DevBuf {
-    void *d = nullptr;
-    size_t cap = 0;
-    cosmica_status reserve(size_t n)
-    {
-        if (n <= cap) return COSMICA_OK;
-        if (d) cudaFree(d);
-        d = nullptr;
-        cap = 0;
-        size_t want = std::max<size_t>(n, 4096);
-        cudaError_t e = cudaMalloc(&d, want);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(scratch)");
-        cap = want;
-        return COSMICA_OK;
-    }
-    void release()
-    {
-        if (d) cudaFree(d);
-        d = nullptr;
-        cap = 0;
-    }
-};
-
-// Pinned staging buffer for the small per-call tables.  Before it is
-// rewritten, the host waits for the previous upload from it to complete.
-struct Staging {
-    void *h = nullptr;
-    size_t cap = 0;
-    cudaEvent_t ev = nullptr;
-    bool pending = false;
-    cosmica_status reserve(size_t n)
-    {
-        if (pending) {
-            cudaError_t e = cudaEventSynchronize(ev);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize(staging)");
-            pending = false;
-        }
-        if (!ev) {
-            cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-        }
-        if (n <= cap) return COSMICA_OK;
-        if (h) cudaFreeHost(h);
-        h = nullptr;
-        cap = 0;
-        size_t want = std::max<size_t>(n, 4096);
-        cudaError_t e = cudaMallocHost(&h, want);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost(staging)");
-        cap = want;
-        return COSMICA_OK;
-    }
-    cosmica_status upload(void *dst, size_t n, cudaStream_t s)
-    {
-        CK(cudaMemcpyAsync(dst, h, n, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(tables)");
-        CK(cudaEventRecord(ev, s), "cudaEventRecord(staging)");
-        pending = true;
-        return COSMICA_OK;
-    }
-    void release()
-    {
-        if (pending && ev) cudaEventSynchronize(ev);
-        if (h) cudaFreeHost(h);
-        if (ev) cudaEventDestroy(ev);
-        h = nullptr;
-        ev = nullptr;
-        cap = 0;
-        pending = false;
-    }
-};
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -324,11 +249,12 @@ PersistentShape shape_for(int acc, const cosmica_tuning *t, uint64_t n_total)
     return PersistentShape{block, (unsigned)grid};
 }
 
-}  // namespace
+}  // namespace host
 
-namespace cosmica {
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launch() { host::g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace cosmica
+
+using namespace cosmica::host;
 
 // =============================================================== model API ==
 struct cosmica_model {

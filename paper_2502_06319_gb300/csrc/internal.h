@@ -28,6 +28,48 @@ struct PersistentShape {
     unsigned grid;
 };
 
+// ---- continuous-batching server -------------------------------------------
+// fresh particles of one (request, energy) slice, offered to one quantum
+struct ServeItem {
+    double T;                  // GeV/n
+    uint64_t first_pid;        // pid of the slice's first particle
+    uint64_t seed;
+    uint64_t exit_idx;         // exit-arena index of the slice's first particle
+    uint32_t slot;             // request slot: parameter set and species index
+    uint32_t energy;           // energy index within the request
+};
+
+// an in-flight particle between two quanta (exact state)
+struct Suspended {
+    union {
+        float f[10];           // compensated pairs (r, th, ph, lnP, s)
+        double d[5];           // FP64 accumulation
+    };
+    uint32_t k, slot, energy, pad;
+    uint64_t pid, seed, exit_idx;
+};
+
+struct ServeArgs {
+    const DevParams *prm;      // per slot
+    const DevSpecies *spc;     // per slot
+    const ServeItem *items;
+    const uint64_t *prefix;
+    uint32_t n_items;
+    uint64_t n_fresh;
+    const Suspended *resume;
+    uint64_t n_resume;
+    Suspended *suspend;
+    unsigned int *n_suspend;
+    unsigned long long *cursors;   // [0] fresh, [1] resume
+    ExitPtrs arena;
+    unsigned int *req_done;        // per slot
+    unsigned long long *req_steps; // per slot
+    uint32_t budget;               // steps per lane per quantum
+};
+
+cudaError_t launch_serve(const ServeArgs &a, int acc, PersistentShape shape, cudaStream_t s);
+int serve_max_blocks_per_sm(int acc, unsigned block);
+
 void note_launch();
 
 cudaError_t launch_derive(DevParams *prm, uint32_t n, cudaStream_t s);

@@ -14,123 +14,12 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "mixed_state.cuh"
 #include "model32.cuh"
 
 namespace cosmica {
 
 namespace {
-
-struct Lane {
-    const F32Params *q;
-    float M2, sq;
-    uint64_t pid, seed, g;
-    uint32_t item, k, max_steps;
-    double R_out;
-};
-
-template <int ACC>
-struct Acc;
-
-// compensated FP32 state
-template <>
-struct Acc<COSMICA_PREC_MIXED> {
-    m32::FF r, th, ph, lnP, s;
-    m32::FF Rout;
-    float r_in2;   // 2 r_in
-    __device__ void init(double r0, double th0, double ph0, double lnP0, double R_out, float r_in)
-    {
-        r = m32::ff_from_double(r0);
-        th = m32::ff_from_double(th0);
-        ph = m32::ff_from_double(ph0);
-        lnP = m32::ff_from_double(lnP0);
-        s.hi = 0.0f; s.lo = 0.0f;
-        Rout = m32::ff_from_double(R_out);
-        r_in2 = 2.0f * r_in;
-    }
-    __device__ float fr() const { return r.hi; }
-    __device__ float fth() const { return th.hi; }
-    __device__ float fph() const { return ph.hi; }
-    __device__ float flnP() const { return lnP.hi; }
-    __device__ void add(float dr, float dth, float dph, float dlnP, float dt)
-    {
-        m32::ff_add(r, dr);
-        m32::ff_add(th, dth);
-        m32::ff_add(ph, dph);
-        m32::ff_add(lnP, dlnP);
-        m32::ff_add(s, dt);
-    }
-    // reflect at r_in, fold theta at the poles, wrap phi; all rare branches
-    __device__ void boundaries(float r_in)
-    {
-        if (r.hi < r_in) {           // r <- 2 r_in - r
-            r.hi = -r.hi; r.lo = -r.lo;
-            m32::ff_add(r, r_in2);
-        }
-        if (th.hi < 0.0f || th.hi > m32::kPiF) fold_theta();
-        if (ph.hi < 0.0f || ph.hi >= m32::kTwoPiF) wrap_phi();
-    }
-    __device__ void fold_theta()
-    {
-        // t = th mod 2 pi in [0, 2pi); if t > pi: th = 2pi - t, ph += pi
-        const double t0 = m32::ff_to_double(th);
-        double t = t0 - kTwoPi * floor(t0 / kTwoPi);
-        if (t > kPi) {
-            t = kTwoPi - t;
-            const double p = m32::ff_to_double(ph) + kPi;
-            ph = m32::ff_from_double(p);
-        }
-        th = m32::ff_from_double(t);
-    }
-    __device__ void wrap_phi()
-    {
-        const double p0 = m32::ff_to_double(ph);
-        ph = m32::ff_from_double(p0 - kTwoPi * floor(p0 / kTwoPi));
-    }
-    __device__ bool exited() const { return m32::ff_ge(r, Rout); }
-    __device__ bool finite() const { return isfinite(r.hi + th.hi + ph.hi + lnP.hi + s.hi); }
-    __device__ void write(const ExitPtrs &out, uint64_t g) const
-    {
-        out.r[g] = m32::ff_to_double(r);
-        out.th[g] = m32::ff_to_double(th);
-        out.ph[g] = m32::ff_to_double(ph);
-        out.lnP[g] = m32::ff_to_double(lnP);
-        out.s[g] = m32::ff_to_double(s);
-    }
-};
-
-// FP64 accumulation of FP32 increments
-template <>
-struct Acc<COSMICA_PREC_MIXED_F64ACC> {
-    double r, th, ph, lnP, s, Rout, r_in;
-    __device__ void init(double r0, double th0, double ph0, double lnP0, double R_out, float r_in_f)
-    {
-        r = r0; th = th0; ph = ph0; lnP = lnP0; s = 0.0; Rout = R_out; r_in = (double)r_in_f;
-    }
-    __device__ float fr() const { return (float)r; }
-    __device__ float fth() const { return (float)th; }
-    __device__ float fph() const { return (float)ph; }
-    __device__ float flnP() const { return (float)lnP; }
-    __device__ void add(float dr, float dth, float dph, float dlnP, float dt)
-    {
-        r += (double)dr; th += (double)dth; ph += (double)dph; lnP += (double)dlnP; s += (double)dt;
-    }
-    __device__ void boundaries(float)
-    {
-        if (r < r_in) r = 2.0 * r_in - r;
-        if (th < 0.0 || th > kPi) {
-            double t = th - kTwoPi * floor(th / kTwoPi);
-            if (t > kPi) { t = kTwoPi - t; ph += kPi; }
-            th = t;
-        }
-        if (ph < 0.0 || ph >= kTwoPi) ph = ph - kTwoPi * floor(ph / kTwoPi);
-    }
-    __device__ bool exited() const { return r >= Rout; }
-    __device__ bool finite() const { return isfinite(r + th + ph + lnP + s); }
-    __device__ void write(const ExitPtrs &out, uint64_t g) const
-    {
-        out.r[g] = r; out.th[g] = th; out.ph[g] = ph; out.lnP[g] = lnP; out.s[g] = s;
-    }
-};
 
 template <int ACC>
 __device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t g, Lane &L, Acc<ACC> &x)
