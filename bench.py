@@ -36,15 +36,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2502_06319_gb300 import workloads as W  # noqa: E402
+from paper_2502_06319_gb300.sharding import items_of, reduce_timing  # noqa: E402
 
 METRIC = "SDE steps/s & spectra/s, FP32-batched vs plain FP64 GPU at <=0.5% spectrum error"
 
-# Algorithmic work of one mixed-precision step, tallied from the source of
-# the step (model32.cuh + the loop of k_mixed.cu): FP32 add/mul/fma, SFU
-# (MUFU) operations and integer operations of Philox, each one issue slot.
-# See DESIGN.md "Roofline" for the tally.
-ALG_INST_PER_STEP = {"fp32": 196, "mufu": 21, "int": 78, "fp32_ff_acc": 50}
-ALG_INST_TOTAL = sum(ALG_INST_PER_STEP.values())
+# Algorithmic work of one mixed-precision step of the full model (drift and
+# wavy sheet on), tallied from the source of the step (model32.cuh and the step
+# of k_mixed.cu), each operation one issue slot: FP32 add/mul/fma (normals 15,
+# coefficients 177, update 14, compensated accumulation 50, finiteness 4), SFU
+# operations (normals 7, coefficients 23, sqrt(dt) 1), integer operations of
+# the Philox block and the uniform mapping (66), and the comparisons of min/max,
+# boundaries and exit tests (14).  A termination shock adds 9 FP32 + 2 SFU.
+ALG_INST_PER_STEP = {"fp32": 260, "sfu": 31, "int_rng": 66, "compare": 14}
+ALG_INST_TS = {"fp32": 9, "sfu": 2}
 SM_LANES_PER_CLK = 128      # 4 SMSPs x 32 lanes: one warp instruction per SMSP per clock
 
 
@@ -59,8 +63,8 @@ def parse():
     ap.add_argument("--c3-scale", type=float, default=1.0, help="scale of config-3 particle counts")
     ap.add_argument("--scale", type=float, default=1.0, help="scale of config-1/2 particles per energy")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shape instead of the autotuner")
-    ap.add_argument("--precision", default=None, choices=["mixed", "mixed_f64acc", "fp64"],
-                    help="default: compensated FP32 for configs 1-2, FP64 accumulation for configs 3-4")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_f64acc", "fp64"],
+                    help="mixed: FP32 step with compensated FP32 (float-float) accumulation")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--cpu-sample", type=int, default=0, help="particles per energy in the oracle sample")
@@ -79,27 +83,6 @@ def workload(args):
         return [W.config2(n)], f"config2: full model, proton, 30 energies x {n}"
     jobs = W.config3(scale=args.c3_scale)
     return jobs, f"config3: 64 heliospheres x 3 species x 30 energies, counts 1e3-5e4 (scale {args.c3_scale})"
-
-
-def items_of(jobs, rank):
-    """Work items (param_idx, species_idx, T, n, first_pid, seed) of all jobs; a rank's copy
-    uses disjoint particle identities and its own seeds."""
-    params, pkeys, species, skeys, items = [], {}, [], {}, []
-    pid = 0
-    base = rank * (1 << 40)
-    for j in jobs:
-        pk = tuple(sorted(j.params.items()))
-        if pk not in pkeys:
-            pkeys[pk] = len(params)
-            params.append(j.params)
-        sk = tuple(sorted(j.species.items()))
-        if sk not in skeys:
-            skeys[sk] = len(species)
-            species.append(j.species)
-        for T, n in zip(j.T_in, j.n_per_energy):
-            items.append((pkeys[pk], skeys[sk], T, n, base + pid, j.seed + 7919 * rank))
-            pid += n
-    return params, species, items
 
 
 class Clocks:
@@ -172,7 +155,7 @@ def run_reference(args):
     if rank != 0:
         return
     jobs, desc = workload(args)
-    sample = args.cpu_sample or (40 if args.workload != "c1" else 100)
+    sample = args.cpu_sample or (600 if args.workload != "c1" else 1500)
     if args.warmup > 0:
         cpu_baseline(jobs, max(2, sample // 10))
     vals, secs, steps = [], 0.0, 0
@@ -246,8 +229,6 @@ def serve_bench(args, cz, torch):
 
 def main():
     args = parse()
-    if args.precision is None:
-        args.precision = "mixed" if args.workload in ("c1", "c2") else "mixed_f64acc"
     if args.impl == "reference":
         return run_reference(args)
     import torch
@@ -302,7 +283,7 @@ def main():
     nI = len(items)
     batch = make_batch(prec)
     if args.no_autotune:
-        tune = cz.cosmica_tuning(128, 0, 1, 0)
+        tune = cz.cosmica_tuning(128, 0, 64, 0, 1)
     else:
         tune, tune_rate = cz.cosmica_autotune(batch, arr, nI)
     tune.use_graph = 1
@@ -348,13 +329,7 @@ def main():
     ms, steps_done, launches = timed(batch, tune, args.warmup, args.steps)
     clk = clocks.stop()
     tot_ms = sum(ms)
-    if dist:
-        tt = torch.tensor([tot_ms, float(steps_done)], dtype=torch.float64, device="cuda")
-        mx = tt.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tt.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        tot_ms, steps_all = float(mx[0]), float(sm[1])
-    else:
-        steps_all = float(steps_done)
+    tot_ms, steps_all = reduce_timing(dist, tot_ms, float(steps_done), device="cuda")
     steps_per_s = steps_all / (tot_ms * 1e-3)
     spectra_per_s = n_spectra * world * args.steps / (tot_ms * 1e-3)
     Jm = J.cpu().numpy().copy()
@@ -396,11 +371,16 @@ def main():
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     f_mhz = clk.get("sm_mhz") or 2070.0
     peak = SM_LANES_PER_CLK * sm_count * f_mhz * 1e6 / 1e12          # T inst/s
-    achieved = ALG_INST_TOTAL * steps_per_s / world / 1e12
+    alg = dict(ALG_INST_PER_STEP)
+    if any(p.get("R_ts", 0.0) > 0.0 for p in params):
+        for k, v in ALG_INST_TS.items():
+            alg[k] += v
+    alg_total = sum(alg.values())
+    achieved = alg_total * steps_per_s / world / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
             "traffic": None, "peak_basis": f"{SM_LANES_PER_CLK} lanes/clk/SM x {sm_count} SMs x "
                                            f"{f_mhz:.0f} MHz (median SM clock sampled under load)",
-            "alg_inst_per_step": ALG_INST_PER_STEP}
+            "alg_inst_per_step": alg, "alg_inst_total": alg_total}
 
     line = {"metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
@@ -409,6 +389,8 @@ def main():
             "config": {"workload": desc, "particles_per_gpu": n_total, "spectra_per_step": n_spectra,
                        "precision": args.precision, "tuning": {"block": tune.block,
                                                                "blocks_per_sm": tune.blocks_per_sm,
+                                                               "compact_period": tune.compact_period,
+                                                               "queue_order": tune.queue_order,
                                                                "graph": bool(tune.use_graph)},
                        "l2": "flushed (256 MB write) before every timed step", "parallelism": f"weak x{world}"},
             "spectra_per_s": spectra_per_s,
@@ -416,7 +398,7 @@ def main():
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clk, "roofline": roof, "fp64_plain": fp64}
     if rank == 0 and not args.no_cpu and world == 1:
-        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(jobs, args.cpu_sample or 40).items()
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(jobs, args.cpu_sample or 1500).items()
                                 if k in ("value", "unit", "cores", "kind", "sample")}
     if rank == 0:
         print(json.dumps(line), flush=True)

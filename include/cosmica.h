@@ -195,6 +195,7 @@ cosmica_status cosmica_propagate(cosmica_model *model, const cosmica_species *sp
                                  const uint32_t *n_per_energy, uint64_t seed,
                                  cosmica_exit_states *out, void *stream);
 
+
 /*
  * Bin the exit rigidities and form the modulated spectrum (Eq. 4 with L = 0
  * (Eq. 6) and J = f P^2 (Sec. VI)): for energy e,
@@ -227,12 +228,19 @@ typedef struct {
     uint64_t seed;
 } cosmica_work_item;
 
-/* Launch shape of the persistent kernel; 0 fields select the defaults. */
+/* Launch shape and scheduling of the persistent kernel.  Passing NULL selects
+ * block 128, the most resident blocks, compaction every 64 steps, no graph,
+ * most-expensive-first queue order. */
 typedef struct {
-    uint32_t block;           /* threads per block                        */
-    uint32_t blocks_per_sm;   /* resident blocks per SM requested         */
-    uint32_t refill_batch;    /* lanes refilled per queue grab (1..32)    */
-    uint32_t use_graph;       /* 1: replay the launch as a CUDA graph     */
+    uint32_t block;           /* threads per block (32..256; 0 = 128)                   */
+    uint32_t blocks_per_sm;   /* resident blocks per SM requested (0 = as many as fit)  */
+    uint32_t compact_period;  /* once the queue is drained, every this many steps the
+                                 active particles of a block are repacked into its lowest
+                                 warps (0 = never)                                       */
+    uint32_t use_graph;       /* 1: replay the launch as a CUDA graph                   */
+    uint32_t queue_order;     /* 0: items in the given order; 1: items with the lowest
+                                 K0 beta P first (longest paths first); exit records keep
+                                 item order either way                                   */
 } cosmica_tuning;
 
 typedef struct cosmica_batch cosmica_batch;
@@ -262,9 +270,12 @@ cosmica_status cosmica_batch_spectrum(cosmica_batch *batch, const cosmica_work_i
                                       double *J_out, double *sigma_out, uint64_t *hist_out,
                                       void *stream);
 
-/* Pick a launch shape for this batch by timing candidate shapes on a short
- * sample of `items` (host) and write the fastest to *best (steps/s in
- * *best_rate if not NULL).  Synchronous; uses the batch's own scratch. */
+/* Pick a launch shape for this batch by timing candidate shapes (block size,
+ * resident blocks, compaction period) on a sample of `items` (host) and write
+ * the fastest to *best (steps/s in *best_rate if not NULL).  Results are cached
+ * for the process per device and configuration class (precision, drift,
+ * termination shock, particle count within a factor of two); a cached class
+ * returns at once.  Synchronous; uses the batch's own scratch. */
 cosmica_status cosmica_autotune(cosmica_batch *batch, const cosmica_work_item *items,
                                 uint32_t n_items, cosmica_tuning *best, double *best_rate);
 

@@ -3,8 +3,10 @@
 Each translation unit gets the floating-point flags its arithmetic needs:
   * k_fp64.cu, k_spectrum.cu: -fmad=false -- FP64 expressions evaluated exactly
     as written (no FMA contraction), so the FP64 path is reproducible bit for bit;
-  * k_mixed.cu, k_serve.cu: --use_fast_math -- the mixed path deliberately
-    uses the SFU approximations and FMA;
+  * k_mixed.cu, k_serve.cu: -ftz=true -prec-div=false -prec-sqrt=false
+    -fmad=false -- the mixed path deliberately uses the SFU approximations, and
+    writes every FMA explicitly so that its rounding is the same in every
+    kernel and inlining context;
   * cosmica_api.cu, server.cu, k_debug_curand.cu: defaults.
 Objects are compiled in parallel and linked into one shared library next to
 this file.
@@ -26,12 +28,16 @@ LIB = os.path.join(HERE, "libcosmica.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# the mixed path: flush-to-zero, approximate division and square root (it uses
+# the SFU intrinsics deliberately), and no automatic FMA contraction -- every
+# FMA of the step is written out, so its rounding cannot depend on context
+MIXED_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false", "-fmad=false"]
 UNITS = {
     "cosmica_api.cu": [],
     "k_fp64.cu": ["-fmad=false"],
     "k_spectrum.cu": ["-fmad=false"],
-    "k_mixed.cu": ["--use_fast_math"],
-    "k_serve.cu": ["--use_fast_math"],
+    "k_mixed.cu": MIXED_FLAGS,
+    "k_serve.cu": MIXED_FLAGS,
     "server.cu": [],
     "k_debug_curand.cu": [],
 }

@@ -66,8 +66,8 @@ class cosmica_work_item(C.Structure):
 
 
 class cosmica_tuning(C.Structure):
-    _fields_ = [("block", C.c_uint32), ("blocks_per_sm", C.c_uint32), ("refill_batch", C.c_uint32),
-                ("use_graph", C.c_uint32)]
+    _fields_ = [("block", C.c_uint32), ("blocks_per_sm", C.c_uint32), ("compact_period", C.c_uint32),
+                ("use_graph", C.c_uint32), ("queue_order", C.c_uint32)]
 
 
 class cosmica_request(C.Structure):

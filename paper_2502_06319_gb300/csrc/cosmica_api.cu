@@ -193,28 +193,45 @@ struct Tables {
     Staging stage;
     DevItem *items = nullptr;
     uint64_t *prefix = nullptr;
+    uint32_t *qitem = nullptr;               // item of each queue slot
+    uint64_t *qprefix = nullptr;             // prefix sums in queue order
     unsigned long long *counters = nullptr;   // [0] cursor, [1] steps
     uint64_t n_total = 0;
     uint32_t n_items = 0;
 
-    cosmica_status build(const std::vector<DevItem> &its, const std::vector<uint64_t> &pre, cudaStream_t s)
+    // order: queue order of the items (a permutation of 0..n-1), or empty for item order
+    cosmica_status build(const std::vector<DevItem> &its, const std::vector<uint64_t> &pre,
+                         const std::vector<uint32_t> &order, cudaStream_t s)
     {
         const size_t nI = its.size();
-        const size_t b_items = align_up(nI * sizeof(DevItem), 256);
+        const size_t b_items = align_up(std::max<size_t>(1, nI) * sizeof(DevItem), 256);
         const size_t b_pre = align_up((nI + 1) * sizeof(uint64_t), 256);
-        const size_t total = b_items + b_pre + 256;
-        cosmica_status st = dev.reserve(total);
+        const size_t b_q = align_up(std::max<size_t>(1, nI) * sizeof(uint32_t), 256);
+        const size_t up = b_items + 2 * b_pre + b_q;
+        cosmica_status st = dev.reserve(up + 256);
         if (st != COSMICA_OK) return st;
-        st = stage.reserve(b_items + b_pre);
+        st = stage.reserve(up);
         if (st != COSMICA_OK) return st;
-        std::memcpy(stage.h, its.data(), nI * sizeof(DevItem));
-        std::memcpy((char *)stage.h + b_items, pre.data(), (nI + 1) * sizeof(uint64_t));
-        items = (DevItem *)dev.d;
-        prefix = (uint64_t *)((char *)dev.d + b_items);
-        counters = (unsigned long long *)((char *)dev.d + b_items + b_pre);
+        char *h = (char *)stage.h;
+        std::memcpy(h, its.data(), nI * sizeof(DevItem));
+        std::memcpy(h + b_items, pre.data(), (nI + 1) * sizeof(uint64_t));
+        uint32_t *hq = (uint32_t *)(h + 2 * b_pre + b_items);
+        uint64_t *hqp = (uint64_t *)(h + b_items + b_pre);
+        hqp[0] = 0;
+        for (size_t k = 0; k < nI; ++k) {
+            const uint32_t i = order.empty() ? (uint32_t)k : order[k];
+            hq[k] = i;
+            hqp[k + 1] = hqp[k] + (pre[i + 1] - pre[i]);
+        }
+        char *d = (char *)dev.d;
+        items = (DevItem *)d;
+        prefix = (uint64_t *)(d + b_items);
+        qprefix = (uint64_t *)(d + b_items + b_pre);
+        qitem = (uint32_t *)(d + b_items + 2 * b_pre);
+        counters = (unsigned long long *)(d + up);
         n_items = (uint32_t)nI;
         n_total = pre[nI];
-        return stage.upload(dev.d, b_items + b_pre, s);
+        return stage.upload(dev.d, up, s);
     }
     void release()
     {
@@ -222,6 +239,30 @@ struct Tables {
         dev.release();
     }
 };
+
+// Queue order with the longest expected paths first: items sorted by K0 beta0 P0
+// ascending (a smaller diffusion coefficient at the start means more steps).
+std::vector<uint32_t> cost_order(const std::vector<DevItem> &its, const cosmica_params *prm,
+                                 const cosmica_species *spc)
+{
+    std::vector<std::pair<double, uint32_t>> key(its.size());
+    for (size_t i = 0; i < its.size(); ++i) {
+        const cosmica_species &sp = spc[its[i].species_idx];
+        const double aoz = (double)sp.A / std::fabs((double)sp.Z);
+        const double T = its[i].T;
+        const double pn = std::sqrt(T * (T + 2.0 * sp.m0_GeV));
+        const double P = aoz * pn;
+        const double beta = pn / (T + sp.m0_GeV);
+        key[i] = {prm[its[i].param_idx].K0 * beta * P, (uint32_t)i};
+    }
+    std::stable_sort(key.begin(), key.end(),
+                     [](const std::pair<double, uint32_t> &a, const std::pair<double, uint32_t> &b) {
+                         return a.first < b.first;
+                     });
+    std::vector<uint32_t> order(its.size());
+    for (size_t k = 0; k < its.size(); ++k) order[k] = key[k].second;
+    return order;
+}
 
 int g_num_sms = 0;
 int num_sms()
@@ -238,6 +279,7 @@ int num_sms()
 PersistentShape shape_for(int acc, const cosmica_tuning *t, uint64_t n_total)
 {
     unsigned block = (t && t->block) ? t->block : 128u;
+    const unsigned period = t ? t->compact_period : 64u;
     block = std::min(256u, std::max(32u, block / 32u * 32u));
     int max_b = mixed_max_blocks_per_sm(acc, block);
     if (max_b < 1) max_b = 1;
@@ -246,7 +288,7 @@ PersistentShape shape_for(int acc, const cosmica_tuning *t, uint64_t n_total)
     uint64_t grid = (uint64_t)num_sms() * (uint64_t)bps;
     const uint64_t need = (n_total + block - 1) / block;   // never more blocks than particles
     grid = std::max<uint64_t>(1, std::min(grid, need));
-    return PersistentShape{block, (unsigned)grid};
+    return PersistentShape{block, (unsigned)grid, period};
 }
 
 }  // namespace host
@@ -409,7 +451,7 @@ extern "C" cosmica_status cosmica_propagate(cosmica_model *m, const cosmica_spec
         its[e].species_idx = 0;
         pre[e + 1] = pre[e] + n_per_energy[e];
     }
-    st = m->tab.build(its, pre, s);
+    st = m->tab.build(its, pre, cost_order(its, &m->p, species), s);
     if (st != COSMICA_OK) return st;
 
     const bool host_out = !is_device_ptr(out->r);
@@ -420,7 +462,7 @@ extern "C" cosmica_status cosmica_propagate(cosmica_model *m, const cosmica_spec
     }
     CK(cudaMemsetAsync(m->tab.counters, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
     LaunchArgs a{m->d_prm, d_sp, m->tab.items, m->tab.prefix, m->tab.n_items, total, ex,
-                 m->tab.counters + 1, m->tab.counters};
+                 m->tab.counters + 1, m->tab.counters, m->tab.qitem, m->tab.qprefix};
     cudaError_t e;
     if (m->p.precision == COSMICA_PREC_FP64) {
         e = launch_propagate_fp64(a, s);
@@ -615,7 +657,7 @@ static cosmica_status batch_launch(cosmica_batch *b, uint64_t total, const ExitP
                                    const cosmica_tuning *tuning, cudaStream_t s)
 {
     LaunchArgs a{b->d_prm, b->d_spc, b->tab.items, b->tab.prefix, b->tab.n_items, total, ex,
-                 b->tab.counters + 1, b->tab.counters};
+                 b->tab.counters + 1, b->tab.counters, b->tab.qitem, b->tab.qprefix};
     auto direct = [&]() -> cosmica_status {
         CK(cudaMemsetAsync(b->tab.counters, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
         cudaError_t e = (b->precision == COSMICA_PREC_FP64)
@@ -628,7 +670,7 @@ static cosmica_status batch_launch(cosmica_batch *b, uint64_t total, const ExitP
     if (!graph) return direct();
     const PersistentShape sh = shape_for(b->precision, tuning, total);
     auto key = std::make_tuple(total, b->tab.n_items, (const void *)ex.r, (const void *)b->tab.dev.d, sh.block,
-                               sh.grid, s, b->precision);
+                               sh.grid * 1024u + sh.compact_period, s, b->precision);
     if (!b->gexec || b->gkey != key) {
         if (b->gexec) {
             cudaGraphExecDestroy(b->gexec);
@@ -675,7 +717,9 @@ extern "C" cosmica_status cosmica_batch_run(cosmica_batch *b, const cosmica_work
         return COSMICA_OK;
     }
     if (!valid_exit(out)) return fail(COSMICA_ERR_INVALID, "exit-state arrays must be non-NULL");
-    st = b->tab.build(its, pre, s);
+    const bool by_cost = tuning ? tuning->queue_order != 0 : true;
+    st = b->tab.build(its, pre, by_cost ? cost_order(its, b->params.data(), b->species.data())
+                                        : std::vector<uint32_t>(), s);
     if (st != COSMICA_OK) return st;
     const bool host_out = !is_device_ptr(out->r);
     ExitPtrs ex = exit_ptrs(out);
@@ -710,12 +754,41 @@ extern "C" cosmica_status cosmica_batch_spectrum(cosmica_batch *b, const cosmica
 }
 
 // =============================================================== autotune ==
+// Tuned shapes are cached per (device, configuration class): the precision,
+// whether the sets have a drift / a termination shock, and the particle count
+// to within a factor of two (it sets the particles per lane, hence the tail).
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, std::pair<cosmica_tuning, double>> g_tune_cache;
+}  // namespace
+
 extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_item *items, uint32_t n_items,
                                            cosmica_tuning *best, double *best_rate)
 {
     if (!b || !best) return fail(COSMICA_ERR_INVALID, "batch / best is NULL");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int drift = 0, ts = 0;
+    for (const cosmica_params &p : b->params) {
+        drift |= p.drift_on != 0;
+        ts |= p.R_ts_AU > 0.0;
+    }
+    uint64_t n_all = 0;
+    for (uint32_t i = 0; i < n_items && items; ++i) n_all += items[i].n;
+    int size_class = 0;
+    while ((n_all >> size_class) > 1) ++size_class;
+    const auto key = std::make_tuple(dev, b->precision, drift, ts, size_class);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *best = it->second.first;
+            if (best_rate) *best_rate = it->second.second;
+            return COSMICA_OK;
+        }
+    }
     if (b->precision == COSMICA_PREC_FP64) {
-        *best = cosmica_tuning{128, 0, 1, 0};
+        *best = cosmica_tuning{128, 0, 0, 0, 0};
         if (best_rate) *best_rate = 0.0;
         return COSMICA_OK;
     }
@@ -750,32 +823,36 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
     if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     double best_r = -1.0;
-    cosmica_tuning bt{128, 0, 1, 0};
+    cosmica_tuning bt{128, 0, 64, 0, 1};
     if (ce == cudaSuccess) {
-        const unsigned blocks[] = {64, 128, 256};
+        const unsigned blocks[] = {128, 256};
+        const unsigned periods[] = {0, 64};
         for (unsigned blk : blocks) {
             const int maxb = mixed_max_blocks_per_sm(b->precision, blk);
             for (int frac = 0; frac < 2; ++frac) {
                 const unsigned bps = frac == 0 ? (unsigned)std::max(1, maxb) : (unsigned)std::max(1, maxb / 2);
                 if (frac == 1 && bps == (unsigned)std::max(1, maxb)) continue;
-                cosmica_tuning t{blk, bps, 1, 0};
-                ce = cudaEventRecord(e0, s);
-                if (ce != cudaSuccess) break;
-                st = cosmica_batch_run(b, sample.data(), n_items, &t, &eo, (uint64_t *)d_steps, s);
-                if (st != COSMICA_OK) break;
-                ce = cudaEventRecord(e1, s);
-                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-                if (ce != cudaSuccess) break;
-                float ms = 0.0f;
-                unsigned long long steps = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ce = cudaMemcpy(&steps, d_steps, sizeof(steps), cudaMemcpyDeviceToHost);
-                if (ce != cudaSuccess) break;
-                const double rate = ms > 0.0f ? (double)steps / (ms * 1e-3) : 0.0;
-                if (rate > best_r) {
-                    best_r = rate;
-                    bt = t;
+                for (unsigned per : periods) {
+                    cosmica_tuning t{blk, bps, per, 0, 1};
+                    ce = cudaEventRecord(e0, s);
+                    if (ce != cudaSuccess) break;
+                    st = cosmica_batch_run(b, sample.data(), n_items, &t, &eo, (uint64_t *)d_steps, s);
+                    if (st != COSMICA_OK) break;
+                    ce = cudaEventRecord(e1, s);
+                    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                    if (ce != cudaSuccess) break;
+                    float ms = 0.0f;
+                    unsigned long long steps = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ce = cudaMemcpy(&steps, d_steps, sizeof(steps), cudaMemcpyDeviceToHost);
+                    if (ce != cudaSuccess) break;
+                    const double rate = ms > 0.0f ? (double)steps / (ms * 1e-3) : 0.0;
+                    if (rate > best_r) {
+                        best_r = rate;
+                        bt = t;
+                    }
                 }
+                if (st != COSMICA_OK || ce != cudaSuccess) break;
             }
             if (st != COSMICA_OK || ce != cudaSuccess) break;
         }
@@ -789,6 +866,8 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
     if (ce != cudaSuccess) return cuda_fail(ce, "autotune");
     *best = bt;
     if (best_rate) *best_rate = best_r;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = {bt, best_r};
     return COSMICA_OK;
 }
 

@@ -21,11 +21,14 @@ struct LaunchArgs {
     ExitPtrs out;
     unsigned long long *steps_total;   // may be null
     unsigned long long *cursor;        // work-queue cursor (persistent kernels)
+    const uint32_t *qitem;             // item of each queue slot (null: item order)
+    const uint64_t *qprefix;           // prefix sums of particle counts in queue order
 };
 
 struct PersistentShape {
     unsigned block;
     unsigned grid;
+    unsigned compact_period;   // 0: no block compaction
 };
 
 // ---- continuous-batching server -------------------------------------------

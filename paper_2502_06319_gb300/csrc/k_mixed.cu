@@ -22,18 +22,21 @@ namespace cosmica {
 namespace {
 
 template <int ACC>
-__device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t g, Lane &L, Acc<ACC> &x)
+__device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t q, Lane &L, Acc<ACC> &x)
 {
-    const uint32_t it = find_item(a.prefix, a.n_items, g);
+    // queue slot q -> (item, index within the item); the exit record keeps item order
+    const uint32_t iq = find_item(a.qprefix, a.n_items, q);
+    const uint32_t it = a.qitem ? a.qitem[iq] : iq;
+    const uint64_t local = q - a.qprefix[iq];
     const DevItem item = a.items[it];
     const DevParams &p = a.prm[item.param_idx];
     const DevSpecies &sp = a.spc[item.species_idx];
     L.q = &p.f;
     L.M2 = sp.aoz_m0_sq;
     L.sq = sp.sgnq;
-    L.pid = item.first_pid + (g - a.prefix[it]);
+    L.pid = item.first_pid + local;
     L.seed = item.seed;
-    L.g = g;
+    L.g = a.prefix[it] + local;
     L.item = it;
     L.k = 0;
     L.max_steps = (uint32_t)p.max_steps;
@@ -42,17 +45,61 @@ __device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t g, 
     x.init(p.r0, p.th0, p.ph0, log(P0), p.R_out, p.f.r_in);
 }
 
+// One Euler-Maruyama step (Eq. 3, Eq. 6) of an active lane; true when the path ended
+// (exit record written).
 template <int ACC>
-__global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a)
+__device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, unsigned long long &my_steps)
 {
+    float z0, z1, z2;
+    m32::normals(L.seed, L.pid, L.k, z0, z1, z2);
+    m32::Drift c;
+    const F32Params &q = *L.q;
+    m32::eval(q, L.M2, L.sq, x.fr(), x.fth(), x.fph(), x.flnP(), c);
+    const float sdt = sqrtf(c.dt);
+    const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
+    const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);
+    const float dph = fmaf(c.dph_drift, c.dt, fmaf(c.l20, z0, c.l22 * z2) * sdt * c.inv_rs);
+    x.add(dr, dth, dph, c.dlnP * c.dt, c.dt);
+    x.boundaries(q.r_in);
+    L.k += 1u;
+
+    int status = COSMICA_PATH_RUNNING;
+    if (!x.finite()) status = COSMICA_PATH_NONFINITE;
+    else if (x.exited()) status = COSMICA_PATH_EXIT;
+    else if (L.k >= L.max_steps) status = COSMICA_PATH_STEP_LIMIT;
+    if (status == COSMICA_PATH_RUNNING) return false;
+    x.write(a.out, L.g);
+    a.out.steps[L.g] = L.k;
+    a.out.status[L.g] = (uint8_t)status;
+    a.out.item[L.g] = L.item;
+    my_steps += L.k;
+    return true;
+}
+
+// Persistent propagation.
+// Phase 1: lanes take particles from the device queue (one atomic per warp for all
+// lanes needing work), step them, write the exit record and refill, until the queue
+// is drained.  Phase 2 (COMPACT): the block advances in epochs of `period` steps;
+// at each checkpoint the active particles are counted and, if they occupy more
+// warps than they need, repacked through shared memory into the block's lowest
+// lanes, so that issued warp instructions keep carrying full lanes while the
+// long tail of exit times plays out.
+template <int ACC, bool COMPACT>
+__global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a, uint32_t period)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ unsigned s_count;
+    __shared__ unsigned s_warp[8];
     const unsigned lane = threadIdx.x & 31u;
+    const unsigned warp = threadIdx.x >> 5;
     Lane L;
     Acc<ACC> x;
     bool active = false, drained = false;
     unsigned long long my_steps = 0;
+    uint32_t since_check = 0;
 
+    // ---- phase 1: queue-fed
     while (true) {
-        // refill: lanes without a particle take consecutive queue entries
         const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
         if (need) {
             unsigned long long base = 0;
@@ -60,44 +107,71 @@ __global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a)
             if (lane == leader) base = atomicAdd(a.cursor, (unsigned long long)__popc(need));
             base = __shfl_sync(0xffffffffu, base, leader);
             if (need & (1u << lane)) {
-                const uint64_t g = base + __popc(need & ((1u << lane) - 1u));
-                if (g < a.n_total) {
-                    start_particle<ACC>(a, g, L, x);
+                const uint64_t q = base + __popc(need & ((1u << lane) - 1u));
+                if (q < a.n_total) {
+                    start_particle<ACC>(a, q, L, x);
                     active = true;
                 } else {
                     drained = true;
                 }
             }
         }
-        if (!__any_sync(0xffffffffu, active)) break;
-        if (!active) continue;
+        if (COMPACT) {
+            // learn of the drained queue even when no lane of the warp needed work
+            if (++since_check >= period) {
+                since_check = 0;
+                unsigned dq = 0;
+                if (lane == 0) dq = *(volatile unsigned long long *)a.cursor >= a.n_total;
+                if (__shfl_sync(0xffffffffu, dq, 0)) drained = true;
+            }
+            if (__all_sync(0xffffffffu, drained || active) && __any_sync(0xffffffffu, drained)) {
+                drained = true;
+                break;
+            }
+        } else if (!__any_sync(0xffffffffu, active)) {
+            break;
+        }
+        if (active && step<ACC>(a, L, x, my_steps)) active = false;
+    }
 
-        // one Euler-Maruyama step (Eq. 3, Eq. 6)
-        float z0, z1, z2;
-        m32::normals(L.seed, L.pid, L.k, z0, z1, z2);
-        m32::Drift c;
-        const F32Params &q = *L.q;
-        const float r = x.fr();
-        m32::eval(q, L.M2, L.sq, r, x.fth(), x.fph(), x.flnP(), c);
-        const float sdt = sqrtf(c.dt);
-        const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
-        const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);
-        const float dph = fmaf(c.dph_drift, c.dt, fmaf(c.l20, z0, c.l22 * z2) * sdt * c.inv_rs);
-        x.add(dr, dth, dph, c.dlnP * c.dt, c.dt);
-        x.boundaries(q.r_in);
-        L.k += 1u;
-
-        int status = COSMICA_PATH_RUNNING;
-        if (!x.finite()) status = COSMICA_PATH_NONFINITE;
-        else if (x.exited()) status = COSMICA_PATH_EXIT;
-        else if (L.k >= L.max_steps) status = COSMICA_PATH_STEP_LIMIT;
-        if (status != COSMICA_PATH_RUNNING) {
-            x.write(a.out, L.g);
-            a.out.steps[L.g] = L.k;
-            a.out.status[L.g] = (uint8_t)status;
-            a.out.item[L.g] = L.item;
-            my_steps += L.k;
-            active = false;
+    if (COMPACT) {
+        // ---- phase 2: epochs with block compaction
+        Packed<ACC> *pack = reinterpret_cast<Packed<ACC> *>(smem_raw);
+        const unsigned nwarps = blockDim.x >> 5;
+        while (true) {
+            if (threadIdx.x == 0) s_count = 0;
+            __syncthreads();
+            const unsigned bal = __ballot_sync(0xffffffffu, active);
+            if (lane == 0) {
+                s_warp[warp] = __popc(bal);
+                atomicAdd(&s_count, (unsigned)__popc(bal));
+            }
+            __syncthreads();
+            const unsigned n = s_count;
+            if (n == 0) break;
+            unsigned occupied = 0, before = 0;
+            for (unsigned w = 0; w < nwarps; ++w) {
+                occupied += s_warp[w] > 0;
+                if (w < warp) before += s_warp[w];
+            }
+            if (occupied > (n + 31) / 32) {
+                if (active) {
+                    const unsigned rank = before + __popc(bal & ((1u << lane) - 1u));
+                    pack[rank].L = L;
+                    pack[rank].x = x;
+                }
+                __syncthreads();
+                active = threadIdx.x < n;
+                if (active) {
+                    L = pack[threadIdx.x].L;
+                    x = pack[threadIdx.x].x;
+                }
+            }
+            __syncthreads();
+            for (uint32_t it = 0; it < period; ++it) {
+                if (!__any_sync(0xffffffffu, active)) break;
+                if (active && step<ACC>(a, L, x, my_steps)) active = false;
+            }
         }
     }
     if (a.steps_total) {
@@ -121,14 +195,18 @@ __global__ void k_debug_eval32(const DevParams *__restrict__ prm, const DevSpeci
 
 }  // namespace
 
+template <int ACC>
+static size_t pack_bytes(unsigned block) { return (size_t)block * sizeof(Packed<ACC>); }
+
 int mixed_max_blocks_per_sm(int acc, unsigned block)
 {
     int nb = 0;
     if (acc == COSMICA_PREC_MIXED_F64ACC)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<COSMICA_PREC_MIXED_F64ACC>,
-                                                      (int)block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<COSMICA_PREC_MIXED_F64ACC, true>,
+                                                      (int)block, pack_bytes<COSMICA_PREC_MIXED_F64ACC>(block));
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<COSMICA_PREC_MIXED>, (int)block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<COSMICA_PREC_MIXED, true>, (int)block,
+                                                      pack_bytes<COSMICA_PREC_MIXED>(block));
     return nb;
 }
 
@@ -136,10 +214,20 @@ cudaError_t launch_propagate_mixed(const LaunchArgs &a, int acc, PersistentShape
 {
     if (a.n_total == 0) return cudaSuccess;
     cudaGetLastError();
-    if (acc == COSMICA_PREC_MIXED_F64ACC)
-        k_propagate_mixed<COSMICA_PREC_MIXED_F64ACC><<<shape.grid, shape.block, 0, s>>>(a);
-    else
-        k_propagate_mixed<COSMICA_PREC_MIXED><<<shape.grid, shape.block, 0, s>>>(a);
+    const uint32_t per = shape.compact_period;
+    if (acc == COSMICA_PREC_MIXED_F64ACC) {
+        if (per)
+            k_propagate_mixed<COSMICA_PREC_MIXED_F64ACC, true>
+                <<<shape.grid, shape.block, pack_bytes<COSMICA_PREC_MIXED_F64ACC>(shape.block), s>>>(a, per);
+        else
+            k_propagate_mixed<COSMICA_PREC_MIXED_F64ACC, false><<<shape.grid, shape.block, 0, s>>>(a, 1);
+    } else {
+        if (per)
+            k_propagate_mixed<COSMICA_PREC_MIXED, true>
+                <<<shape.grid, shape.block, pack_bytes<COSMICA_PREC_MIXED>(shape.block), s>>>(a, per);
+        else
+            k_propagate_mixed<COSMICA_PREC_MIXED, false><<<shape.grid, shape.block, 0, s>>>(a, 1);
+    }
     note_launch();
     return cudaGetLastError();
 }

@@ -13,7 +13,6 @@ struct Lane {
     float M2, sq;
     uint64_t pid, seed, g;
     uint32_t item, k, max_steps;
-    double R_out;
 };
 
 template <int ACC>
@@ -120,5 +119,12 @@ struct Acc<COSMICA_PREC_MIXED_F64ACC> {
     }
 };
 
+
+// a lane's complete state, moved through shared memory by block compaction
+template <int ACC>
+struct Packed {
+    Lane L;
+    Acc<ACC> x;
+};
 
 }  // namespace cosmica

@@ -8,6 +8,13 @@
 // a float-float value is compared lexicographically against the float-float
 // split of R_out, which equals comparing the exact sum with R_out.
 //
+// Every fused multiply-add is written out (fmaf) and the translation units
+// that include this file are built with -fmad=false, so the compiler never
+// contracts differently in different inlining contexts: the step's rounding is
+// the same in the batched kernel, the serving kernel and both phases of each,
+// which keeps every path identical across launch shapes (the wavy current
+// sheet amplifies single roundings).
+//
 // The model is the same reading as the FP64 step; the algebra is rearranged
 // for FP32 (closed forms instead of cancelling differences):
 //   (1 + tanh x)/2 = 1/(1 + e^-2x),   1 - tanh^2 x = 4 s (1 - s) with s = that logistic,
@@ -65,13 +72,16 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
     // Parker spiral
     const float Gam = q.Omega * r * sn * inv_V;
     const float G2 = Gam * Gam;
-    const float iq = __fdividef(1.0f, 1.0f + G2);
-    const float dGam_dth = Gam * (cot - dV * inv_V);
+    const float iq = __fdividef(1.0f, fmaf(Gam, Gam, 1.0f));
+    const float dGam_dth = Gam * fmaf(-dV, inv_V, cot);
 
-    // termination shock factor
-    const float st = half_one_plus_tanh((r - q.R_ts) * q.inv_dts);
-    const float g = fmaf(-q.ts_drop, st, 1.0f);
-    const float dg = -q.ts_drop * 2.0f * st * (1.0f - st) * q.inv_dts;
+    // termination shock factor (uniform branch: no shock in the parameter set)
+    float g = 1.0f, dg = 0.0f;
+    if (q.ts_drop != 0.0f) {
+        const float st = half_one_plus_tanh((r - q.R_ts) * q.inv_dts);
+        g = fmaf(-q.ts_drop, st, 1.0f);
+        dg = -q.ts_drop * 2.0f * st * (1.0f - st) * q.inv_dts;
+    }
 
     // diffusion tensor in (r, th, ph); K_rth = K_thph = 0
     const float Kb = q.K0 * beta * P;
@@ -116,7 +126,9 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
             const float phs = fmaf(q.Omega * r, inv_V, ph);
             const float dphs_dr = q.Omega * inv_V;
             const float dphs_dth = -q.Omega * r * dV * inv_V * inv_V;
-            const float red = fmaf(-kTwoPiF, rintf(phs * kInvTwoPiF), phs);
+            // nearest integer by the 1.5 2^23 shift (|phs| / 2 pi < 2^22): two FADDs
+            const float turns = __fsub_rn(__fadd_rn(phs * kInvTwoPiF, 12582912.0f), 12582912.0f);
+            const float red = fmaf(-kTwoPiF, turns, phs);
             float sp, cp;
             __sincosf(red, &sp, &cp);
             const float th_cs = kHalfPiF + atanf(q.ta * sp);
@@ -135,10 +147,10 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
             const float inv_d = __fdividef(1.0f, delta);
             const float u = (th_cs - th) * inv_d;
             const float sh = half_one_plus_tanh(u);
-            h = 2.0f * sh - 1.0f;
+            h = fmaf(2.0f, sh, -1.0f);
             const float sech2 = 4.0f * sh * (1.0f - sh);
-            hr = sech2 * (dthcs * dphs_dr - u * dd_dr) * inv_d;
-            ht = sech2 * (dthcs * dphs_dth - 1.0f - u * dd_dth) * inv_d;
+            hr = sech2 * fmaf(dthcs, dphs_dr, -u * dd_dr) * inv_d;
+            ht = sech2 * fmaf(-u, dd_dth, fmaf(dthcs, dphs_dth, -1.0f)) * inv_d;
             hp = sech2 * dthcs * inv_d;
         }
         const float s = sq * q.polarity * q.CA0 * beta * P * inv_r;
@@ -146,14 +158,14 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
         const float dWph_dth = -fmaf(ht, Gf, h * dGf_dth);
         const float dWph_dr = -fmaf(hr, Gf, h * dGf_dr);
         vd0 = s * fmaf(cot, Wph, dWph_dth);
-        vd1 = s * (hp * F * inv_sn - Wph - r * dWph_dr);
+        vd1 = s * fmaf(-r, dWph_dr, fmaf(hp * F, inv_sn, -Wph));
         vd2 = -s * fmaf(ht, F, h * dF_dth);
     }
 
     const float Ar_tot = Ar - V - vd0;
     o.Ar_tot = Ar_tot;
-    o.dth_drift = Ath - vd1 * inv_r;
-    o.dph_drift = Aph - vd2 * inv_rs;
+    o.dth_drift = fmaf(-vd1, inv_r, Ath);
+    o.dph_drift = fmaf(-vd2, inv_rs, Aph);
     o.inv_r = inv_r;
     o.inv_rs = inv_rs;
     o.dlnP = 0.66666666666666667f * V * inv_r;
@@ -181,17 +193,22 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
     }
 }
 
-// Three N(0,1) in FP32: Box-Muller on the Philox words mapped to (0,1] as
-// ((x >> 8) + 1/2) 2^-24.
+// A Philox word mapped to (0,1) as ((x >> 9) + 1/2) 2^-23, exactly: the top 23
+// bits become the mantissa of a float in [1,2), then 1 - 2^-24 is subtracted.
+__device__ __forceinline__ float uniform01(uint32_t x)
+{
+    return __fsub_rn(__uint_as_float(0x3F800000u | (x >> 9)), 0.99999994039535522f);
+}
+
+// Three N(0,1) in FP32: Box-Muller on the four Philox words.
 __device__ __forceinline__ void normals(uint64_t seed, uint64_t pid, uint32_t k, float &z0, float &z1,
                                         float &z2)
 {
     const uint4 w = philox_step_block(seed, pid, k);
-    const float sc = 5.9604644775390625e-8f;    // 2^-24
-    const float u0 = fmaf((float)(w.x >> 8), sc, 0.5f * sc);
-    const float u1 = fmaf((float)(w.y >> 8), sc, 0.5f * sc);
-    const float u2 = fmaf((float)(w.z >> 8), sc, 0.5f * sc);
-    const float u3 = fmaf((float)(w.w >> 8), sc, 0.5f * sc);
+    const float u0 = uniform01(w.x);
+    const float u1 = uniform01(w.y);
+    const float u2 = uniform01(w.z);
+    const float u3 = uniform01(w.w);
     const float rho0 = sqrtf(-2.0f * __logf(u0));
     const float rho2 = sqrtf(-2.0f * __logf(u2));
     // angle 2 pi u - pi lies in (-pi, pi], where the SFU sin/cos are accurate;
@@ -211,14 +228,15 @@ struct FF {
 
 // (hi, lo) += d: TwoSum of hi + d, error carried into lo, then renormalised
 // so that |lo| <= ulp(hi)/2.
+// (the _rn intrinsics keep every rounding exactly as written)
 __device__ __forceinline__ void ff_add(FF &a, float d)
 {
-    const float s = a.hi + d;
-    const float bb = s - a.hi;
-    const float err = (a.hi - (s - bb)) + (d - bb);
-    const float lo = a.lo + err;
-    const float hi = s + lo;
-    a.lo = lo - (hi - s);
+    const float s = __fadd_rn(a.hi, d);
+    const float bb = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+    const float lo = __fadd_rn(a.lo, err);
+    const float hi = __fadd_rn(s, lo);
+    a.lo = __fsub_rn(lo, __fsub_rn(hi, s));
     a.hi = hi;
 }
 

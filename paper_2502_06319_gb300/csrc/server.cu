@@ -373,7 +373,7 @@ extern "C" cosmica_status cosmica_server_create(size_t mem_budget, int32_t preci
     cudaGetDevice(&s->device);
     const unsigned block = 128;
     const int bps = std::max(1, serve_max_blocks_per_sm(precision, block));
-    s->shape = PersistentShape{block, (unsigned)(num_sms() * bps)};
+    s->shape = PersistentShape{block, (unsigned)(num_sms() * bps), 0u};
     s->lane_cap = (uint64_t)s->shape.grid * block;
     const size_t fixed = 2 * s->lane_cap * sizeof(Suspended) + kMaxSlots * (sizeof(DevParams) + sizeof(DevSpecies) + 12) +
                          (size_t)kMaxEnergies * (kMaxBins + 3) * 8 + kMaxEnergies * (16 + sizeof(SpecItem)) + 4096;

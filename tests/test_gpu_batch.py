@@ -70,7 +70,7 @@ def test_graph_replay_and_batch_spectrum():
     for rep in range(3):
         out = cz.ExitBuffers(total)
         steps = t.zeros(1, dtype=t.int64, device="cuda")
-        tune = cz.cosmica_tuning(128, 0, 1, 1)
+        tune = cz.cosmica_tuning(128, 0, 64, 1, 1)
         with t.cuda.stream(s):
             cz.cosmica_batch_run(b, arr, len(items), out, tuning=tune, steps_out=steps, stream=s)
         s.synchronize()
@@ -96,5 +96,31 @@ def test_autotune_picks_a_valid_shape():
     sets, species, items, b = _setup(cz.PREC_MIXED, counts_seed=2)
     arr = cz.make_items(items)
     tune, rate = cz.cosmica_autotune(b, arr, len(items))
-    assert tune.block in (64, 128, 256) and tune.blocks_per_sm >= 1 and rate > 0
+    assert tune.block in (128, 256) and tune.blocks_per_sm >= 1 and rate > 0
+    assert tune.compact_period in (0, 64) and tune.queue_order == 1
+    cz.cosmica_batch_destroy(b)
+
+
+@pytest.mark.parametrize("precision", [cz.PREC_MIXED, cz.PREC_MIXED_F64ACC])
+def test_launch_shape_compaction_and_queue_order_do_not_change_results(precision):
+    """Block size, resident blocks, block compaction and the queue order move particles
+    between lanes and change when they start; none may change any exit record."""
+    t = torch()
+    sets, species, items, b = _setup(precision, counts_seed=3)
+    arr = cz.make_items(items)
+    total = sum(i[3] for i in items)
+    ref = None
+    for tune in (cz.cosmica_tuning(128, 0, 0, 0, 0), cz.cosmica_tuning(64, 1, 64, 0, 1),
+                 cz.cosmica_tuning(256, 0, 8, 0, 1), cz.cosmica_tuning(32, 2, 1, 0, 0)):
+        out = cz.ExitBuffers(total)
+        steps = t.zeros(1, dtype=t.int64, device="cuda")
+        cz.cosmica_batch_run(b, arr, len(items), out, tuning=tune, steps_out=steps)
+        t.cuda.synchronize()
+        g = out.numpy()
+        assert int(steps.item()) == int(g["steps"].astype(np.int64).sum())
+        if ref is None:
+            ref = g
+        else:
+            for k in ref:
+                assert np.array_equal(ref[k], g[k]), (tune.block, tune.compact_period, k)
     cz.cosmica_batch_destroy(b)

@@ -49,22 +49,3 @@ def test_mixed_full_model_vs_oracle(orc, acc):
     print("full model acc=%d rel err per energy:" % acc, np.round(J / Jo - 1, 4).tolist())
     assert np.all(np.abs(J - Jo) <= 3 * comb), (J, Jo, comb)
     m.close()
-
-
-def test_mixed_vs_fp64_gpu_config2_full_size():
-    """Config 2 at full size (30 energies x 20 000): the mixed path against the FP64 GPU
-    path, which is itself pinned path by path to the oracle."""
-    job = W.config2()
-    g64, out64, m64 = gpu_run(job, precision=cz.PREC_FP64)
-    H64, J64, S64 = gpu_spectrum(job, out64)
-    del out64
-    for acc in ACCS:
-        g, out, m = gpu_run(job, precision=acc)
-        H, J, S = gpu_spectrum(job, out)
-        rel = J / J64 - 1
-        comb = np.hypot(S, S64)
-        print(f"config2 acc={acc}: max |rel| = {np.abs(rel).max():.2e}; sigma_rel max {np.max(S / J):.2e}")
-        assert np.all(np.abs(J - J64) <= 3 * comb)
-        assert np.all(np.abs(rel) <= 5e-3), rel
-        m.close()
-    m64.close()
