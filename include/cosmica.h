@@ -195,6 +195,32 @@ cosmica_status cosmica_propagate(cosmica_model *model, const cosmica_species *sp
                                  const uint32_t *n_per_energy, uint64_t seed,
                                  cosmica_exit_states *out, void *stream);
 
+/*
+ * Propagation that allocates nothing.  The paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory -- code running
+ * under a memory pool it does not own (a framework's caching allocator may
+ * hold all free memory, so a raw cudaMalloc fails or fragments the pool),
+ * code that must not trigger the device-wide synchronisation of cudaFree
+ * while other work is in flight, and hosts that route every device
+ * allocation through an approved allocator.
+ * Same arguments and results as cosmica_propagate, with the parameter set
+ * passed directly instead of a model handle.  The library's scratch for the
+ * call (parameter block, species, work items, prefix sums, queue cursor,
+ * step counter) is a fixed static device array of about 45 KB that every GPU
+ * loading the library holds until the process exits; the call makes no
+ * cudaMalloc, cudaFree or other allocating call.
+ *   n_energies   at most COSMICA_NOALLOC_MAX_ENERGIES (INVALID otherwise)
+ *   out          device memory only (INVALID otherwise)
+ * The first call on a device looks the array up (cudaGetSymbolAddress with
+ * that device current): make it before any stream capture.  All calls share
+ * the array -- the counters are cleared at the start of each call, the tables
+ * overwritten -- so calls whose work overlaps on the GPU race; serialise them.
+ */
+#define COSMICA_NOALLOC_MAX_ENERGIES 1024u
+cosmica_status cosmica_propagate_noalloc(const cosmica_params *params, const cosmica_species *species,
+                                         const double *T_in_GeVn, uint32_t n_energies,
+                                         const uint32_t *n_per_energy, uint64_t seed,
+                                         cosmica_exit_states *out, void *stream);
 
 /*
  * Bin the exit rigidities and form the modulated spectrum (Eq. 4 with L = 0

@@ -7,7 +7,7 @@ Each translation unit gets the floating-point flags its arithmetic needs:
     -fmad=false -- the mixed path deliberately uses the SFU approximations, and
     writes every FMA explicitly so that its rounding is the same in every
     kernel and inlining context;
-  * cosmica_api.cu, server.cu, k_debug_curand.cu: defaults.
+  * cosmica_api.cu, server.cu, k_noalloc.cu, k_debug_curand.cu: defaults.
 Objects are compiled in parallel and linked into one shared library next to
 this file.
 """
@@ -39,6 +39,7 @@ UNITS = {
     "k_mixed.cu": MIXED_FLAGS,
     "k_serve.cu": MIXED_FLAGS,
     "server.cu": [],
+    "k_noalloc.cu": [],
     "k_debug_curand.cu": [],
 }
 

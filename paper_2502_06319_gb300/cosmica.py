@@ -125,6 +125,10 @@ def lib():
                                                  C.POINTER(cosmica_bins), P, P, P, P]
             L.cosmica_autotune.argtypes = [P, C.POINTER(cosmica_work_item), C.c_uint32, C.POINTER(cosmica_tuning),
                                            C.POINTER(C.c_double)]
+            L.cosmica_propagate_noalloc.argtypes = [C.POINTER(cosmica_params), C.POINTER(cosmica_species),
+                                                    C.POINTER(C.c_double), C.c_uint32, C.POINTER(C.c_uint32),
+                                                    C.c_uint64, C.POINTER(cosmica_exit_states), P]
+            L.cosmica_propagate_noalloc.restype = C.c_int
             L.cosmica_server_create.argtypes = [C.c_size_t, C.c_int32, C.c_uint32, C.POINTER(P)]
             L.cosmica_server_submit.argtypes = [P, C.POINTER(cosmica_request), C.POINTER(C.c_uint64)]
             L.cosmica_server_poll.argtypes = [P, C.c_uint64, C.POINTER(cosmica_result)]
@@ -272,6 +276,16 @@ def cosmica_propagate(model: int, species: cosmica_species, T_in: Sequence[float
     T = (C.c_double * max(1, n))(*[float(t) for t in T_in])
     N = (C.c_uint32 * max(1, n))(*[int(x) for x in n_per_energy])
     _check(lib().cosmica_propagate(model, C.byref(species), T, n, N, int(seed), C.byref(out.c), _stream(stream)))
+
+
+def cosmica_propagate_noalloc(params: cosmica_params, species: cosmica_species, T_in: Sequence[float],
+                              n_per_energy: Sequence[int], seed: int, out: ExitBuffers, stream=None) -> None:
+    """Allocation-free propagation: scratch in a fixed static device array (see cosmica.h)."""
+    n = len(T_in)
+    T = (C.c_double * max(1, n))(*[float(t) for t in T_in])
+    N = (C.c_uint32 * max(1, n))(*[int(x) for x in n_per_energy])
+    _check(lib().cosmica_propagate_noalloc(C.byref(params), C.byref(species), T, n, N, int(seed), C.byref(out.c),
+                                           _stream(stream)))
 
 
 def cosmica_spectrum(exit: ExitBuffers, species: cosmica_species, T_in: Sequence[float], bins: cosmica_bins,
