@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shape instead of the autotuner")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_f64acc", "fp64"],
                     help="mixed: FP32 step with compensated FP32 (float-float) accumulation")
+    ap.add_argument("--formulation", default="momentum", choices=["momentum", "energy"],
+                    help="momentum form (Eq. 5-6, the method) or the energy form of Eq. 1 with loss weights "
+                         "(configs 1-2 only)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--cpu-sample", type=int, default=0, help="particles per energy in the oracle sample")
@@ -267,6 +270,13 @@ def main():
             print(json.dumps(line), flush=True)
         return
     jobs, desc = workload(args)
+    energy = args.formulation == "energy"
+    if energy:
+        if args.workload not in ("c1", "c2"):
+            raise SystemExit("--formulation energy applies to configs 1-2")
+        for j in jobs:
+            j.params = dict(j.params, formulation=1.0)
+        desc += ", energy formulation (Eq. 1, loss-weighted Eq. 4)"
     prec = {"mixed": cz.PREC_MIXED, "mixed_f64acc": cz.PREC_MIXED_F64ACC, "fp64": cz.PREC_FP64}[args.precision]
     params, species, items = items_of(jobs, rank)
     n_total = sum(i[3] for i in items)
@@ -287,16 +297,21 @@ def main():
     else:
         tune, tune_rate = cz.cosmica_autotune(batch, arr, nI)
     tune.use_graph = 1
-    out = cz.ExitBuffers(n_total)
+    out = cz.ExitBuffers(n_total, with_lw=energy)
     J = torch.empty(nI, dtype=torch.float64, device="cuda")
     S = torch.empty_like(J)
     H = torch.empty(nI * (nb + 3), dtype=torch.int64, device="cuda")
     steps_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
 
+    sp0 = cz.make_species(jobs[0].species)
+
     def one_pass(b, t):
         cz.cosmica_batch_run(b, arr, nI, out, tuning=t, steps_out=steps_dev, stream=stream)
-        cz.cosmica_batch_spectrum(b, arr, nI, out, bins, J, S, H, stream=stream)
+        if energy:   # loss-weighted Eq. 4 (items are the energies of one job, in exit order)
+            cz.cosmica_spectrum_unbinned(out, sp0, jobs[0].T_in, jobs[0].n_per_energy, 1, J, S, stream=stream)
+        else:
+            cz.cosmica_batch_spectrum(b, arr, nI, out, bins, J, S, H, stream=stream)
 
     def timed(b, t, warm, k):
         with torch.cuda.stream(stream):
@@ -387,7 +402,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff" if prec == cz.PREC_MIXED else
             ("f32+f64acc" if prec == cz.PREC_MIXED_F64ACC else "f64"), "data": "synthetic",
             "config": {"workload": desc, "particles_per_gpu": n_total, "spectra_per_step": n_spectra,
-                       "precision": args.precision, "tuning": {"block": tune.block,
+                       "precision": args.precision, "formulation": args.formulation, "tuning": {"block": tune.block,
                                                                "blocks_per_sm": tune.blocks_per_sm,
                                                                "compact_period": tune.compact_period,
                                                                "queue_order": tune.queue_order,

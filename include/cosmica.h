@@ -120,6 +120,12 @@ typedef struct {
     double r0_AU, th0_rad, ph0_rad;   /* detection point (start of the backward paths) */
     uint32_t max_steps;        /* step limit per path (>= 1)               */
     int32_t precision;         /* COSMICA_PREC_*                           */
+    int32_t formulation;       /* 0: momentum form (Eq. 5-6, L = 0); 1: energy
+                                  form (Eq. 1: kinetic energy T integrated with
+                                  A_T = (2/3)(V/r) alpha T and the loss
+                                  L = (2V/(3r))(1 + beta^2) accumulated for the
+                                  weight of Eq. 4; needs exit->lw)              */
+    int32_t reserved0;
 } cosmica_params;
 
 /* Particle species: mass number A, signed charge number Z, rest mass per
@@ -141,6 +147,9 @@ typedef struct {
     uint8_t *status;                 /* COSMICA_PATH_*                           */
     uint32_t *item;                  /* work item (energy index for propagate)   */
     uint64_t n;
+    double *lw;                      /* optional: log of the loss weight
+                                        exp(-sum L ds) of Eq. 4 (energy form; 0 for
+                                        the momentum form); NULL = not written   */
 } cosmica_exit_states;
 
 /* Local interstellar spectrum per GeV/n (Sec. II.B, Eq. 4).
@@ -224,8 +233,9 @@ cosmica_status cosmica_propagate_noalloc(const cosmica_params *params, const cos
 
 /*
  * Bin the exit rigidities and form the modulated spectrum (Eq. 4 with L = 0
- * (Eq. 6) and J = f P^2 (Sec. VI)): for energy e,
- *   J(T0) = (P0^2/beta0) (1/N) sum_b c_b w_b,  w_b = J_LIS(T_b) beta_b / P_b^2
+ * (Eq. 6) and J = f P^2 (Sec. VI), J the intensity per unit kinetic energy,
+ * f conserved along each path): for energy e,
+ *   J(T0) = P0^2 (1/N) sum_b c_b w_b,  w_b = J_LIS(T_b) / P_b^2
  * at the log-centre P_b of each bin; sigma = sample standard deviation of the
  * summand / sqrt(N).  Only EXIT paths inside [P_min, P_max) enter N.
  *   exit           device exit states (item = energy index)
@@ -238,6 +248,23 @@ cosmica_status cosmica_spectrum(const cosmica_exit_states *exit, const cosmica_s
                                 const cosmica_lis *lis, const cosmica_bins *bins,
                                 double *J_out, double *sigma_out, uint64_t *hist_out,
                                 void *stream);
+
+/*
+ * Unbinned Eq. 4 per energy, every exit rigidity weighted exactly:
+ *   formulation 0 (momentum form, L = 0):  J(T0) = P0^2 <J_LIS(T_ex) / P_ex^2>
+ *   formulation 1 (energy form, Eq. 1):    J(T0) = beta0 <J_LIS(T_ex) exp(lw) / beta_ex>
+ * (Eq. 1 is written for the density per unit kinetic energy U = 4 pi J / v; the
+ * loss weight exp(lw) = exp(-sum L ds) is read from exit->lw).  sigma = sample
+ * standard deviation of the summand / sqrt(N); only EXIT paths enter N.
+ *   exit          device exit states; energy e owns the n_per_energy[e] entries
+ *                 after those of energies 0..e-1 (the order cosmica_propagate writes)
+ *   n_per_energy  host [n_energies]
+ *   J_out, sigma_out  device [n_energies] (NaN where N = 0)
+ * Sums are reduced in a fixed order, so the result is deterministic. */
+cosmica_status cosmica_spectrum_unbinned(const cosmica_exit_states *exit, const cosmica_species *species,
+                                         const double *T_in_GeVn, uint32_t n_energies,
+                                         const uint32_t *n_per_energy, int32_t formulation,
+                                         const cosmica_lis *lis, double *J_out, double *sigma_out, void *stream);
 
 /* ---------------- batched persistent launch (many heliospheres) ---------------- */
 

@@ -92,6 +92,8 @@ typedef struct {
     double r0;            /* AU, start radius                                    */
     double th0;           /* rad, start colatitude                               */
     double ph0;           /* rad, start longitude                                */
+    double formulation;   /* 0: momentum form (Eq. 5-6, L = 0); 1: energy form
+                             (Eq. 1: T-SDE with the loss weight of Eq. 4)         */
 } orc_params;
 
 typedef struct {
@@ -655,6 +657,8 @@ void orc_eval(const orc_params *p, const orc_species *sp,
 /* ======================================================================= */
 typedef struct {
     double r, th, ph, lnP, s;
+    double T, Lam;        /* energy form: kinetic energy per nucleon, loss integral */
+    double r_old;         /* radius at the start of the step */
     uint32_t k;
     int status;
 } orc_state;
@@ -663,6 +667,7 @@ static void em_step(const orc_params *p, const orc_species *sp, uint64_t seed, u
                     orc_state *x, double *dt_out)
 {
     double z[3];
+    x->r_old = x->r;
     orc_normals(seed, pid, x->k, 0u, z);
     orc_coef c;
     eval_coef(p, sp, x->r, x->th, x->ph, x->lnP, &c);
@@ -680,7 +685,19 @@ static void em_step(const orc_params *p, const orc_species *sp, uint64_t seed, u
     x->r = x->r + dr;
     x->th = x->th + dth;
     x->ph = x->ph + dph;
-    x->lnP = x->lnP + dlnP;
+    if (p->formulation != 0.0) {
+        /* Eq. 1 backward: A_T = (1/3) div V alpha T = (2/3)(V/r) alpha T,
+         * alpha = (T + 2 m0)/(T + m0); loss L = div V - (1/3) div V d(alpha T)/dT
+         * = (2V/(3r)) (1 + beta^2), accumulated for the weight exp(-sum L ds) of Eq. 4 */
+        double alpha = (x->T + 2.0 * sp->m0) / (x->T + sp->m0);
+        double A_T = 2.0 * c.V / (3.0 * x->r_old) * alpha * x->T;
+        double Lloss = 2.0 * c.V / (3.0 * x->r_old) * (1.0 + c.beta * c.beta);
+        x->T = x->T + A_T * dt;
+        x->Lam = x->Lam + Lloss * dt;
+        x->lnP = orc_log(sp->A / fabs(sp->Z) * sqrt(x->T * (x->T + 2.0 * sp->m0)));
+    } else {
+        x->lnP = x->lnP + dlnP;
+    }
     /* reflecting inner boundary */
     if (x->r < p->r_in) x->r = 2.0 * p->r_in - x->r;
     /* fold th into [0, pi]; crossing a pole shifts ph by pi */
@@ -716,6 +733,7 @@ static void init_state(const orc_params *p, const orc_species *sp, double T_in, 
 {
     x->r = p->r0; x->th = p->th0; x->ph = p->ph0;
     x->lnP = orc_log(rigidity(sp, T_in));
+    x->T = T_in; x->Lam = 0.0;
     x->s = 0.0; x->k = 0u; x->status = ORC_RUNNING;
 }
 
@@ -726,7 +744,7 @@ void orc_run_particles(const orc_params *prm, const orc_species *spc, uint64_t n
                        const uint32_t *prm_idx, const uint32_t *sp_idx, const double *T_in,
                        const uint64_t *pid, const uint64_t *seed,
                        double *r, double *th, double *ph, double *lnP, double *s,
-                       uint32_t *steps, uint8_t *status, int nthreads)
+                       uint32_t *steps, uint8_t *status, double *lw, int nthreads)
 {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -740,6 +758,7 @@ void orc_run_particles(const orc_params *prm, const orc_species *spc, uint64_t n
         while (x.status == ORC_RUNNING) em_step(p, sp, seed[i], pid[i], &x, 0);
         r[i] = x.r; th[i] = x.th; ph[i] = x.ph; lnP[i] = x.lnP; s[i] = x.s;
         steps[i] = x.k; status[i] = (uint8_t)x.status;
+        lw[i] = -x.Lam;
     }
 }
 

@@ -8,9 +8,11 @@ What each function follows:
   * ``expand``      -- one quasi-particle per (energy bin, sample index) (Sec. IV.A);
   * ``run``         -- the backward Euler-Maruyama loop of Eq. 3 with Eq. 6 (C side);
   * ``histogram``   -- exit rigidities binned on log-spaced bins (Sec. IV.A, binning);
-  * ``spectrum``    -- Eq. 4 with L = 0 (Eq. 6) and J = f P^2 (Sec. VI): since f is
-                       conserved along a path, f(r0, P0) = <f_LIS(P_exit)>, i.e.
-                       J(T0) = (P0^2/beta0) <J_LIS(T_exit) beta_exit / P_exit^2>.
+  * ``spectrum``    -- Eq. 4 with L = 0 (Eq. 6) and J = f P^2 (Sec. VI), J the intensity
+                       per unit kinetic energy: f is conserved along a path, so
+                       f(r0, P0) = <f_LIS(P_exit)> and J(T0) = P0^2 <J_LIS(T_exit) / P_exit^2>.
+                       (The energy formulation, Eq. 1 with the loss weight of Eq. 4,
+                       gives the same expectation: see ``spectrum_energy_form``.)
 """
 from __future__ import annotations
 
@@ -32,7 +34,7 @@ PARAM_FIELDS = (
     "lat_fast_deg", "tilt_deg", "polarity", "drift_on", "hcs_on", "R_out", "R_ts",
     "ts_K_factor", "r_in", "dt_max", "dt_fixed", "max_steps", "isotropic",
     "V_const_kms", "eps_adv", "eps_diff", "dt_min", "dlat_deg", "dts_AU",
-    "dcs_min_deg", "rot_period_day", "r0", "th0", "ph0",
+    "dcs_min_deg", "rot_period_day", "r0", "th0", "ph0", "formulation",
 )
 
 EXIT, STEP_LIMIT, NONFINITE = 1, 2, 3
@@ -91,7 +93,7 @@ def lib():
             L.orc_eval_n.restype = C.c_int
             L.orc_run_particles.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcSpecies), C.c_uint64,
                                             u32p, u32p, f64p, u64p, u64p,
-                                            f64p, f64p, f64p, f64p, f64p, u32p, u8p, C.c_int]
+                                            f64p, f64p, f64p, f64p, f64p, u32p, u8p, f64p, C.c_int]
             L.orc_trace.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcSpecies), C.c_double,
                                     C.c_uint64, C.c_uint64, C.c_uint32, f64p]
             L.orc_trace.restype = C.c_int
@@ -182,12 +184,13 @@ def run_particles(param_sets, species_list, prm_idx, sp_idx, T, pid, seed, threa
     out = {k: np.empty(n, np.float64) for k in ("r", "th", "ph", "lnP", "s")}
     out["steps"] = np.empty(n, np.uint32)
     out["status"] = np.empty(n, np.uint8)
+    out["lw"] = np.empty(n, np.float64)
     lib().orc_run_particles(prm, spc, n,
                             np.ascontiguousarray(prm_idx, np.uint32), np.ascontiguousarray(sp_idx, np.uint32),
                             np.ascontiguousarray(T, np.float64), np.ascontiguousarray(pid, np.uint64),
                             np.ascontiguousarray(seed, np.uint64),
                             out["r"], out["th"], out["ph"], out["lnP"], out["s"], out["steps"],
-                            out["status"], int(threads))
+                            out["status"], out["lw"], int(threads))
     return out
 
 
@@ -246,13 +249,14 @@ def bin_centres(P_min: float, P_max: float, nbins: int) -> np.ndarray:
 
 
 def spectrum_from_hist(H: np.ndarray, species: dict, T_in, P_min: float, P_max: float, nbins: int):
-    """Binned Eq. 4: J(T0) = (P0^2/beta0) (1/N) sum_b c_b w_b, w_b = J_LIS(T_b) beta_b / P_b^2,
-    sigma = sample std of the summand / sqrt(N).  Under/overflow and failed paths are excluded."""
+    """Binned Eq. 4: J(T0) = P0^2 (1/N) sum_b c_b w_b, w_b = J_LIS(T_b) / P_b^2 at the bin's
+    log-centre, sigma = sample std of the summand / sqrt(N).  Under/overflow and failed paths
+    are excluded."""
     T_in = np.asarray(T_in, np.float64)
     Pb = bin_centres(P_min, P_max, nbins)
-    w = lis(kinetic(species, Pb)) * beta(species, Pb) / Pb ** 2
+    w = lis(kinetic(species, Pb)) / Pb ** 2
     P0 = rigidity(species, T_in)
-    pref = P0 ** 2 / beta(species, P0)
+    pref = P0 ** 2
     J = np.zeros(len(T_in))
     S = np.zeros(len(T_in))
     for e in range(len(T_in)):
@@ -273,9 +277,9 @@ def spectrum_unbinned(run_out: dict, species: dict, T_in):
     T_in = np.asarray(T_in, np.float64)
     ok = run_out["status"] == EXIT
     P = np.exp(run_out["lnP"])
-    wt = lis(kinetic(species, P)) * beta(species, P) / P ** 2
+    wt = lis(kinetic(species, P)) / P ** 2
     P0 = rigidity(species, T_in)
-    pref = P0 ** 2 / beta(species, P0)
+    pref = P0 ** 2
     J = np.full(len(T_in), math.nan)
     S = np.full(len(T_in), math.nan)
     for e in range(len(T_in)):
@@ -285,6 +289,26 @@ def spectrum_unbinned(run_out: dict, species: dict, T_in):
         x = wt[m]
         J[e] = pref[e] * x.mean()
         S[e] = pref[e] * (x.std(ddof=1) / math.sqrt(len(x)) if len(x) > 1 else 0.0)
+    return J, S
+
+
+def spectrum_energy_form(run_out: dict, species: dict, T_in):
+    """Eq. 4 for the energy formulation (Eq. 1): U = 4 pi J / v is the density per unit
+    kinetic energy, so J(T0) / beta0 = <J_LIS(T_exit) exp(-sum L ds) / beta_exit>."""
+    T_in = np.asarray(T_in, np.float64)
+    ok = run_out["status"] == EXIT
+    P = np.exp(run_out["lnP"])
+    wt = lis(kinetic(species, P)) * np.exp(run_out["lw"]) / beta(species, P)
+    b0 = beta(species, rigidity(species, T_in))
+    J = np.full(len(T_in), math.nan)
+    S = np.full(len(T_in), math.nan)
+    for e in range(len(T_in)):
+        m = ok & (run_out["energy"] == e)
+        if m.sum() == 0:
+            continue
+        x = wt[m]
+        J[e] = b0[e] * x.mean()
+        S[e] = b0[e] * (x.std(ddof=1) / math.sqrt(len(x)) if len(x) > 1 else 0.0)
     return J, S
 
 

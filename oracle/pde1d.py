@@ -15,8 +15,8 @@ rigidity: with tau = lnP_top - lnP,
 
 started from f = f_LIS at lnP_top (modulation is negligible at 10^4 GV) and
 integrated with Crank-Nicolson in tau and second-order central differences in
-r.  The modulated spectrum per kinetic energy follows from J = f P^2 (Sec. VI)
-with dT/dP = beta |Z| / A:  J(T0) = (P0^2 / beta0) f(r0, P0).
+r.  The modulated intensity per kinetic energy follows from J = f P^2 (Sec. VI):
+J(T0) = P0^2 f(r0, P0), with f_LIS = J_LIS / P^2 at the boundary.
 
 The Monte Carlo estimator of Eq. 4 computes exactly this quantity, so the two
 must agree to within the Euler-Maruyama step bias plus Monte Carlo error.
@@ -44,9 +44,9 @@ def _beta_T(species, P):
 
 
 def f_lis(species, P):
-    """Phase-space density at the boundary, up to a constant: J_LIS(T) beta / P^2."""
+    """Phase-space density at the boundary, up to a constant: J_LIS(T) / P^2."""
     b, T = _beta_T(species, P)
-    return lis(T) * b / P ** 2
+    return lis(T) / P ** 2
 
 
 def solve(species, K0, V_kms, r_in, R, r0, P0_list, n_r=1200, dlnP=2e-3, P_top=1e4):
@@ -109,8 +109,7 @@ def solve(species, K0, V_kms, r_in, R, r0, P0_list, n_r=1200, dlnP=2e-3, P_top=1
         k0 = int(math.floor(k))
         t = k - k0
         fr0 = f_at_r0[k0] * (1 - t) + f_at_r0[k0 + 1] * t
-        b0, _ = _beta_T(species, P0)
-        out.append(P0 ** 2 / b0 * fr0)
+        out.append(P0 ** 2 * fr0)
     return np.asarray(out)
 
 

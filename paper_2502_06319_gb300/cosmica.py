@@ -38,7 +38,8 @@ class cosmica_params(C.Structure):
         ("eps_adv", C.c_double), ("eps_diff", C.c_double), ("V_const_kms", C.c_double),
         ("dlat_deg", C.c_double), ("dts_AU", C.c_double), ("dcs_min_deg", C.c_double),
         ("rot_period_day", C.c_double), ("r0_AU", C.c_double), ("th0_rad", C.c_double), ("ph0_rad", C.c_double),
-        ("max_steps", C.c_uint32), ("precision", C.c_int32),
+        ("max_steps", C.c_uint32), ("precision", C.c_int32), ("formulation", C.c_int32),
+        ("reserved0", C.c_int32),
     ]
 
 
@@ -49,7 +50,7 @@ class cosmica_species(C.Structure):
 class cosmica_exit_states(C.Structure):
     _fields_ = [("r", C.c_void_p), ("th", C.c_void_p), ("ph", C.c_void_p), ("lnP", C.c_void_p),
                 ("s", C.c_void_p), ("steps", C.c_void_p), ("status", C.c_void_p), ("item", C.c_void_p),
-                ("n", C.c_uint64)]
+                ("n", C.c_uint64), ("lw", C.c_void_p)]
 
 
 class cosmica_lis(C.Structure):
@@ -115,6 +116,10 @@ def lib():
             L.cosmica_spectrum.argtypes = [C.POINTER(cosmica_exit_states), C.POINTER(cosmica_species),
                                            C.POINTER(C.c_double), C.c_uint32, C.POINTER(cosmica_lis),
                                            C.POINTER(cosmica_bins), P, P, P, P]
+            L.cosmica_spectrum_unbinned.argtypes = [C.POINTER(cosmica_exit_states), C.POINTER(cosmica_species),
+                                                    C.POINTER(C.c_double), C.c_uint32, C.POINTER(C.c_uint32),
+                                                    C.c_int32, C.POINTER(cosmica_lis), P, P, P]
+            L.cosmica_spectrum_unbinned.restype = C.c_int
             L.cosmica_batch_create.argtypes = [C.POINTER(cosmica_params), C.c_uint32, C.POINTER(cosmica_species),
                                                C.c_uint32, C.POINTER(P)]
             L.cosmica_batch_destroy.argtypes = [P]
@@ -186,8 +191,9 @@ _PARAM_MAP = {
     "eps_adv": "eps_adv", "eps_diff": "eps_diff", "V_const_kms": "V_const_kms", "dlat_deg": "dlat_deg",
     "dts_AU": "dts_AU", "dcs_min_deg": "dcs_min_deg", "rot_period_day": "rot_period_day",
     "r0": "r0_AU", "th0": "th0_rad", "ph0": "ph0_rad", "max_steps": "max_steps",
+    "formulation": "formulation",
 }
-_INT_FIELDS = {"polarity", "drift_on", "hcs_on", "isotropic", "max_steps"}
+_INT_FIELDS = {"polarity", "drift_on", "hcs_on", "isotropic", "max_steps", "formulation"}
 
 
 def make_params(d: dict, precision: int = PREC_FP64) -> cosmica_params:
@@ -211,7 +217,7 @@ def make_bins(P_min: float, P_max: float, n: int) -> cosmica_bins:
 class ExitBuffers:
     """Exit-state SoA (torch tensors) and its ctypes view."""
 
-    def __init__(self, n: int, device="cuda", pin_memory: bool = False):
+    def __init__(self, n: int, device="cuda", pin_memory: bool = False, with_lw: bool = False):
         import torch
         kw = dict(device=device)
         if device == "cpu" and pin_memory:
@@ -225,14 +231,18 @@ class ExitBuffers:
         self.steps = torch.empty(self.n, dtype=torch.int32, **kw)    # uint32 bits
         self.status = torch.empty(self.n, dtype=torch.uint8, **kw)
         self.item = torch.empty(self.n, dtype=torch.int32, **kw)     # uint32 bits
+        self.lw = torch.empty(self.n, dtype=torch.float64, **kw) if with_lw else None
         self.c = cosmica_exit_states(*[_ptr(t) for t in (self.r, self.th, self.ph, self.lnP, self.s,
-                                                         self.steps, self.status, self.item)], self.n)
+                                                         self.steps, self.status, self.item)], self.n,
+                                     _ptr(self.lw))
 
     def numpy(self) -> dict:
         import numpy as np
         out = {k: getattr(self, k).cpu().numpy() for k in ("r", "th", "ph", "lnP", "s", "status")}
         out["steps"] = self.steps.cpu().numpy().view(np.uint32)
         out["item"] = self.item.cpu().numpy().view(np.uint32)
+        if self.lw is not None:
+            out["lw"] = self.lw.cpu().numpy()
         return out
 
     @property
@@ -295,6 +305,17 @@ def cosmica_spectrum(exit: ExitBuffers, species: cosmica_species, T_in: Sequence
     lp = C.byref(lis) if lis is not None else None
     _check(lib().cosmica_spectrum(C.byref(exit.c), C.byref(species), T, n, lp, C.byref(bins), _ptr(J),
                                   _ptr(sigma), _ptr(hist), _stream(stream)))
+
+
+def cosmica_spectrum_unbinned(exit: ExitBuffers, species: cosmica_species, T_in: Sequence[float],
+                              n_per_energy: Sequence[int], formulation: int, J, sigma,
+                              lis: Optional[cosmica_lis] = None, stream=None) -> None:
+    n = len(T_in)
+    T = (C.c_double * max(1, n))(*[float(t) for t in T_in])
+    N = (C.c_uint32 * max(1, n))(*[int(x) for x in n_per_energy])
+    lp = C.byref(lis) if lis is not None else None
+    _check(lib().cosmica_spectrum_unbinned(C.byref(exit.c), C.byref(species), T, n, N, int(formulation), lp,
+                                           _ptr(J), _ptr(sigma), _stream(stream)))
 
 
 # --------------------------------------------------------------- batch API --

@@ -51,6 +51,7 @@ struct DevParams {
     double drift_on, hcs_on, isotropic;
     double R_out, R_ts, ts_f, r_in, dt_max, dt_fixed, dt_min, eps_adv, eps_diff;
     double V_const_kms, dlat_deg, dts, dcs_min_deg, rot_period, r0, th0, ph0, max_steps;
+    double formulation;        // 0 momentum form, 1 energy form
     int32_t precision, pad;
     // derived on the device
     double B0;                 // nT, |B|(1 AU, equator) = B1AU
@@ -77,6 +78,7 @@ struct ExitPtrs {
     uint32_t *steps;
     uint8_t *status;
     uint32_t *item;
+    double *lw;                // log loss weight (energy form), may be null
 };
 
 // Index of the work item owning global particle g: prefix[i] <= g < prefix[i+1].

@@ -84,6 +84,8 @@ cosmica_status check_params(const cosmica_params *p)
     if (p->max_steps < 1) return fail(COSMICA_ERR_INVALID, "max_steps must be >= 1");
     if (p->precision < COSMICA_PREC_FP64 || p->precision > COSMICA_PREC_MIXED_F64ACC)
         return fail(COSMICA_ERR_INVALID, "unknown precision %d", p->precision);
+    if (p->formulation != 0 && p->formulation != 1)
+        return fail(COSMICA_ERR_INVALID, "formulation %d: 0 (momentum) or 1 (energy)", p->formulation);
     if (!p->isotropic) {
         if (!(pos(p->V_slow_kms) && pos(p->V_fast_kms) && pos(p->B1AU_nT) && pos(p->rot_period_day) &&
               pos(p->dlat_deg)))
@@ -122,6 +124,7 @@ DevParams to_dev(const cosmica_params &p)
     d.eps_adv = p.eps_adv; d.eps_diff = p.eps_diff; d.V_const_kms = p.V_const_kms;
     d.dlat_deg = p.dlat_deg; d.dts = p.dts_AU; d.dcs_min_deg = p.dcs_min_deg; d.rot_period = p.rot_period_day;
     d.r0 = p.r0_AU; d.th0 = p.th0_rad; d.ph0 = p.ph0_rad; d.max_steps = (double)p.max_steps;
+    d.formulation = (double)p.formulation;
     d.precision = p.precision;
     return d;
 }
@@ -147,19 +150,24 @@ bool valid_exit(const cosmica_exit_states *o)
 
 ExitPtrs exit_ptrs(const cosmica_exit_states *o)
 {
-    return ExitPtrs{o->r, o->th, o->ph, o->lnP, o->s, o->steps, o->status, o->item};
+    return ExitPtrs{o->r, o->th, o->ph, o->lnP, o->s, o->steps, o->status, o->item, o->lw};
 }
 
 // Device exit buffers standing in for host-resident outputs.
 struct ExitStage {
     DevBuf buf;
-    cosmica_status make(uint64_t n, ExitPtrs &d)
+    cosmica_status make(uint64_t n, ExitPtrs &d, bool with_lw = false)
     {
-        // eight arrays, each starting on a 256-byte boundary
+        // up to nine arrays, each starting on a 256-byte boundary
         const size_t a8 = align_up(n * 8, 256), a4 = align_up(n * 4, 256), a1 = align_up(n, 256);
-        cosmica_status st = buf.reserve(5 * a8 + 2 * a4 + a1);
+        cosmica_status st = buf.reserve((with_lw ? 6 : 5) * a8 + 2 * a4 + a1);
         if (st != COSMICA_OK) return st;
         char *p = (char *)buf.d;
+        d.lw = nullptr;
+        if (with_lw) {
+            d.lw = (double *)p;
+            p += a8;
+        }
         d.r = (double *)p;   p += a8;
         d.th = (double *)p;  p += a8;
         d.ph = (double *)p;  p += a8;
@@ -181,6 +189,7 @@ struct ExitStage {
         CK(cudaMemcpyAsync(o->steps, d.steps, n * 4, cudaMemcpyDeviceToHost, s), "D2H steps");
         CK(cudaMemcpyAsync(o->item, d.item, n * 4, cudaMemcpyDeviceToHost, s), "D2H item");
         CK(cudaMemcpyAsync(o->status, d.status, n, cudaMemcpyDeviceToHost, s), "D2H status");
+        if (o->lw && d.lw) CK(cudaMemcpyAsync(o->lw, d.lw, n * 8, cudaMemcpyDeviceToHost, s), "D2H lw");
         CK(cudaStreamSynchronize(s), "cudaStreamSynchronize(host exit states)");
         return COSMICA_OK;
     }
@@ -281,7 +290,7 @@ PersistentShape shape_for(int acc, const cosmica_tuning *t, uint64_t n_total)
     unsigned block = (t && t->block) ? t->block : 128u;
     const unsigned period = t ? t->compact_period : 64u;
     block = std::min(256u, std::max(32u, block / 32u * 32u));
-    int max_b = mixed_max_blocks_per_sm(acc, block);
+    int max_b = mixed_max_blocks_per_sm(acc, block, period != 0);
     if (max_b < 1) max_b = 1;
     int bps = (t && t->blocks_per_sm) ? (int)t->blocks_per_sm : max_b;
     bps = std::min(bps, max_b);
@@ -454,10 +463,11 @@ extern "C" cosmica_status cosmica_propagate(cosmica_model *m, const cosmica_spec
     st = m->tab.build(its, pre, cost_order(its, &m->p, species), s);
     if (st != COSMICA_OK) return st;
 
+    if (m->p.formulation == 1 && !out->lw) return fail(COSMICA_ERR_INVALID, "the energy form needs out->lw");
     const bool host_out = !is_device_ptr(out->r);
     ExitPtrs ex = exit_ptrs(out);
     if (host_out) {
-        st = m->exit_stage.make(total, ex);
+        st = m->exit_stage.make(total, ex, out->lw != nullptr);
         if (st != COSMICA_OK) return st;
     }
     CK(cudaMemsetAsync(m->tab.counters, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
@@ -467,7 +477,8 @@ extern "C" cosmica_status cosmica_propagate(cosmica_model *m, const cosmica_spec
     if (m->p.precision == COSMICA_PREC_FP64) {
         e = launch_propagate_fp64(a, s);
     } else {
-        e = launch_propagate_mixed(a, m->p.precision, shape_for(m->p.precision, nullptr, total), s);
+        e = launch_propagate_mixed(a, m->p.precision, m->p.formulation == 1,
+                                   shape_for(m->p.precision, nullptr, total), s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
     if (host_out) return ExitStage::copy_back(ex, out, s);
@@ -565,6 +576,51 @@ extern "C" cosmica_status cosmica_spectrum(const cosmica_exit_states *exit, cons
                         (cudaStream_t)stream);
 }
 
+extern "C" cosmica_status cosmica_spectrum_unbinned(const cosmica_exit_states *exit, const cosmica_species *species,
+                                                    const double *T_in, uint32_t n_energies,
+                                                    const uint32_t *n_per_energy, int32_t formulation,
+                                                    const cosmica_lis *lis, double *J_out, double *sigma_out,
+                                                    void *stream)
+{
+    cosmica_status st = check_species(species);
+    if (st != COSMICA_OK) return st;
+    if (formulation != 0 && formulation != 1) return fail(COSMICA_ERR_INVALID, "formulation %d", formulation);
+    if (n_energies == 0) return COSMICA_OK;
+    if (!T_in || !n_per_energy || !exit || !J_out || !sigma_out) return fail(COSMICA_ERR_INVALID, "NULL argument");
+    uint64_t total = 0;
+    for (uint32_t e = 0; e < n_energies; ++e) total += n_per_energy[e];
+    if (exit->n != total) return fail(COSMICA_ERR_INVALID, "exit->n != sum(n_per_energy)");
+    if (formulation == 1 && !exit->lw) return fail(COSMICA_ERR_INVALID, "the energy form needs exit->lw");
+    if (total > 0 && (!valid_exit(exit) || !is_device_ptr(exit->lnP)))
+        return fail(COSMICA_ERR_INVALID, "exit states must be device memory");
+    if (!is_device_ptr(J_out) || !is_device_ptr(sigma_out)) return fail(COSMICA_ERR_INVALID, "J / sigma must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    thread_local DevBuf buf, lbuf;
+    thread_local Staging stage, lstage;
+    const size_t b_items = align_up(n_energies * sizeof(SpecItem), 256);
+    const size_t bytes = b_items + (n_energies + 1) * sizeof(uint64_t);
+    st = buf.reserve(bytes);
+    if (st != COSMICA_OK) return st;
+    st = stage.reserve(bytes);
+    if (st != COSMICA_OK) return st;
+    SpecItem *hi = (SpecItem *)stage.h;
+    uint64_t *hp = (uint64_t *)((char *)stage.h + b_items);
+    hp[0] = 0;
+    for (uint32_t e = 0; e < n_energies; ++e) {
+        hi[e] = SpecItem{T_in[e], (double)species->A, (double)species->Z, species->m0_GeV};
+        hp[e + 1] = hp[e] + n_per_energy[e];
+    }
+    st = stage.upload(buf.d, bytes, s);
+    if (st != COSMICA_OK) return st;
+    int kind; const double *lnT, *lnJ; uint32_t ln;
+    st = upload_lis(lis, lbuf, lstage, s, &kind, &lnT, &lnJ, &ln);
+    if (st != COSMICA_OK) return st;
+    cudaError_t e = launch_spectrum_unbinned(exit_ptrs(exit), (const uint64_t *)((char *)buf.d + b_items), n_energies,
+                                             (const SpecItem *)buf.d, formulation, kind, lnT, lnJ, ln, J_out,
+                                             sigma_out, s);
+    return e == cudaSuccess ? COSMICA_OK : cuda_fail(e, "unbinned spectrum launch");
+}
+
 // =============================================================== batch API ==
 struct cosmica_batch {
     std::vector<cosmica_params> params;
@@ -594,6 +650,8 @@ extern "C" cosmica_status cosmica_batch_create(const cosmica_params *params, uin
         if (st != COSMICA_OK) return st;
         if (params[i].precision != params[0].precision)
             return fail(COSMICA_ERR_INVALID, "all parameter sets of a batch must share one precision");
+        if (params[i].formulation != params[0].formulation)
+            return fail(COSMICA_ERR_INVALID, "all parameter sets of a batch must share one formulation");
     }
     for (uint32_t i = 0; i < n_species; ++i) {
         cosmica_status st = check_species(species + i);
@@ -662,14 +720,15 @@ static cosmica_status batch_launch(cosmica_batch *b, uint64_t total, const ExitP
         CK(cudaMemsetAsync(b->tab.counters, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
         cudaError_t e = (b->precision == COSMICA_PREC_FP64)
                             ? launch_propagate_fp64(a, s)
-                            : launch_propagate_mixed(a, b->precision, shape_for(b->precision, tuning, total), s);
+                            : launch_propagate_mixed(a, b->precision, b->params[0].formulation == 1,
+                                                     shape_for(b->precision, tuning, total), s);
         if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
         return COSMICA_OK;
     };
     const bool graph = tuning && tuning->use_graph && s != nullptr;
     if (!graph) return direct();
     const PersistentShape sh = shape_for(b->precision, tuning, total);
-    auto key = std::make_tuple(total, b->tab.n_items, (const void *)ex.r, (const void *)b->tab.dev.d, sh.block,
+    auto key = std::make_tuple(total, b->tab.n_items, (const void *)ex.lw, (const void *)b->tab.dev.d, sh.block,
                                sh.grid * 1024u + sh.compact_period, s, b->precision);
     if (!b->gexec || b->gkey != key) {
         if (b->gexec) {
@@ -721,10 +780,12 @@ extern "C" cosmica_status cosmica_batch_run(cosmica_batch *b, const cosmica_work
     st = b->tab.build(its, pre, by_cost ? cost_order(its, b->params.data(), b->species.data())
                                         : std::vector<uint32_t>(), s);
     if (st != COSMICA_OK) return st;
+    if (b->params[0].formulation == 1 && !out->lw)
+        return fail(COSMICA_ERR_INVALID, "the energy form needs out->lw");
     const bool host_out = !is_device_ptr(out->r);
     ExitPtrs ex = exit_ptrs(out);
     if (host_out) {
-        st = b->exit_stage.make(total, ex);
+        st = b->exit_stage.make(total, ex, out->lw != nullptr);
         if (st != COSMICA_OK) return st;
     }
     st = batch_launch(b, total, ex, tuning, s);
@@ -810,11 +871,11 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
     ExitPtrs ex;
     {
         ExitStage tmp;
-        st = tmp.make(total, ex);
+        st = tmp.make(total, ex, b->params[0].formulation == 1);
         if (st != COSMICA_OK) return st;
         out_buf = tmp.buf;
     }
-    cosmica_exit_states eo{ex.r, ex.th, ex.ph, ex.lnP, ex.s, ex.steps, ex.status, ex.item, total};
+    cosmica_exit_states eo{ex.r, ex.th, ex.ph, ex.lnP, ex.s, ex.steps, ex.status, ex.item, total, ex.lw};
     unsigned long long *d_steps = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -827,34 +888,32 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
     if (ce == cudaSuccess) {
         const unsigned blocks[] = {128, 256};
         const unsigned periods[] = {0, 64};
+        std::vector<cosmica_tuning> cands;
         for (unsigned blk : blocks) {
-            const int maxb = mixed_max_blocks_per_sm(b->precision, blk);
-            for (int frac = 0; frac < 2; ++frac) {
-                const unsigned bps = frac == 0 ? (unsigned)std::max(1, maxb) : (unsigned)std::max(1, maxb / 2);
-                if (frac == 1 && bps == (unsigned)std::max(1, maxb)) continue;
-                for (unsigned per : periods) {
-                    cosmica_tuning t{blk, bps, per, 0, 1};
-                    ce = cudaEventRecord(e0, s);
-                    if (ce != cudaSuccess) break;
-                    st = cosmica_batch_run(b, sample.data(), n_items, &t, &eo, (uint64_t *)d_steps, s);
-                    if (st != COSMICA_OK) break;
-                    ce = cudaEventRecord(e1, s);
-                    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-                    if (ce != cudaSuccess) break;
-                    float ms = 0.0f;
-                    unsigned long long steps = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    ce = cudaMemcpy(&steps, d_steps, sizeof(steps), cudaMemcpyDeviceToHost);
-                    if (ce != cudaSuccess) break;
-                    const double rate = ms > 0.0f ? (double)steps / (ms * 1e-3) : 0.0;
-                    if (rate > best_r) {
-                        best_r = rate;
-                        bt = t;
-                    }
-                }
-                if (st != COSMICA_OK || ce != cudaSuccess) break;
+            for (unsigned per : periods) {
+                const unsigned maxb = (unsigned)std::max(1, mixed_max_blocks_per_sm(b->precision, blk, per != 0));
+                cands.push_back(cosmica_tuning{blk, maxb, per, 0, 1});
+                if (maxb / 2 >= 1 && maxb / 2 != maxb) cands.push_back(cosmica_tuning{blk, maxb / 2, per, 0, 1});
             }
-            if (st != COSMICA_OK || ce != cudaSuccess) break;
+        }
+        for (const cosmica_tuning &t : cands) {
+            ce = cudaEventRecord(e0, s);
+            if (ce != cudaSuccess) break;
+            st = cosmica_batch_run(b, sample.data(), n_items, &t, &eo, (uint64_t *)d_steps, s);
+            if (st != COSMICA_OK) break;
+            ce = cudaEventRecord(e1, s);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) break;
+            float ms = 0.0f;
+            unsigned long long steps = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ce = cudaMemcpy(&steps, d_steps, sizeof(steps), cudaMemcpyDeviceToHost);
+            if (ce != cudaSuccess) break;
+            const double rate = ms > 0.0f ? (double)steps / (ms * 1e-3) : 0.0;
+            if (rate > best_r) {
+                best_r = rate;
+                bt = t;
+            }
         }
     }
     if (e0) cudaEventDestroy(e0);

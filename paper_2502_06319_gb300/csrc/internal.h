@@ -79,8 +79,8 @@ cudaError_t launch_derive(DevParams *prm, uint32_t n, cudaStream_t s);
 cudaError_t launch_propagate_fp64(const LaunchArgs &a, cudaStream_t s);
 
 // mixed precision persistent kernel; acc = COSMICA_PREC_MIXED or COSMICA_PREC_MIXED_F64ACC
-cudaError_t launch_propagate_mixed(const LaunchArgs &a, int acc, PersistentShape shape, cudaStream_t s);
-int mixed_max_blocks_per_sm(int acc, unsigned block);
+cudaError_t launch_propagate_mixed(const LaunchArgs &a, int acc, bool energy, PersistentShape shape, cudaStream_t s);
+int mixed_max_blocks_per_sm(int acc, unsigned block, bool compact);
 
 cudaError_t launch_histogram(const ExitPtrs &ex, uint64_t n, uint32_t n_items, uint32_t nbins, double x_lo,
                              double dx, unsigned long long *hist, cudaStream_t s);
@@ -92,6 +92,10 @@ cudaError_t launch_spectrum(const unsigned long long *hist, uint32_t n_items, ui
                             double x_lo, double dx, const SpecItem *items, int lis_kind,
                             const double *lis_lnT, const double *lis_lnJ, uint32_t lis_n,
                             double *J, double *sigma, cudaStream_t s);
+
+cudaError_t launch_spectrum_unbinned(const ExitPtrs &ex, const uint64_t *prefix, uint32_t n_items,
+                                     const SpecItem *items, int form, int lis_kind, const double *lis_lnT,
+                                     const double *lis_lnJ, uint32_t lis_n, double *J, double *sigma, cudaStream_t s);
 
 cudaError_t launch_debug_eval64(const DevParams *prm, const DevSpecies *spc, uint32_t n, const double *st,
                                 double *out, cudaStream_t s);

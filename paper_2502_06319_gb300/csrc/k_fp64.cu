@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(128) k_propagate_fp64(const DevParams *__restr
         out.steps[g] = x.k;
         out.status[g] = (uint8_t)x.status;
         out.item[g] = it;
+        if (out.lw) out.lw[g] = -x.Lam;
         my_steps = x.k;
     }
     if (steps_total) {

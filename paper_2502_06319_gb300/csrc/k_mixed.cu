@@ -21,8 +21,9 @@ namespace cosmica {
 
 namespace {
 
-template <int ACC>
-__device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t q, Lane &L, Acc<ACC> &x)
+template <int ACC, bool EN>
+__device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t q, Lane &L, Acc<ACC> &x,
+                                               EnergyAcc<ACC, EN> &en)
 {
     // queue slot q -> (item, index within the item); the exit record keeps item order
     const uint32_t iq = find_item(a.qprefix, a.n_items, q);
@@ -43,23 +44,41 @@ __device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t q, 
     const double T = item.T;
     const double P0 = sp.A / fabs(sp.Z) * sqrt(T * (T + 2.0 * sp.m0));
     x.init(p.r0, p.th0, p.ph0, log(P0), p.R_out, p.f.r_in);
+    en.init(T, (float)sp.m0, sp.aoz);
 }
 
 // One Euler-Maruyama step (Eq. 3, Eq. 6) of an active lane; true when the path ended
 // (exit record written).
-template <int ACC>
-__device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, unsigned long long &my_steps)
+template <int ACC, bool EN>
+__device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, EnergyAcc<ACC, EN> &en,
+                                     unsigned long long &my_steps)
 {
     float z0, z1, z2;
     m32::normals(L.seed, L.pid, L.k, z0, z1, z2);
     m32::Drift c;
     const F32Params &q = *L.q;
-    m32::eval(q, L.M2, L.sq, x.fr(), x.fth(), x.fph(), x.flnP(), c);
+    float lnP;
+    if constexpr (EN) {
+        // rigidity from the integrated kinetic energy: P = (A/|Z|) sqrt(T (T + 2 m0))
+        const float T = en.fT();
+        lnP = __logf(en.aoz * sqrtf(T * (T + 2.0f * en.m0)));
+    } else {
+        lnP = x.flnP();
+    }
+    m32::eval(q, L.M2, L.sq, x.fr(), x.fth(), x.fph(), lnP, c);
     const float sdt = sqrtf(c.dt);
     const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
     const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);
     const float dph = fmaf(c.dph_drift, c.dt, fmaf(c.l20, z0, c.l22 * z2) * sdt * c.inv_rs);
-    x.add(dr, dth, dph, c.dlnP * c.dt, c.dt);
+    if constexpr (EN) {
+        // Eq. 1 backward: A_T = (2/3)(V/r) alpha T, loss L = (2V/(3r)) (1 + beta^2)
+        const float T = en.fT();
+        const float alpha = __fdividef(T + 2.0f * en.m0, T + en.m0);
+        en.add(c.dlnP * alpha * T * c.dt, c.dlnP * fmaf(c.beta, c.beta, 1.0f) * c.dt);
+        x.add(dr, dth, dph, 0.0f, c.dt);
+    } else {
+        x.add(dr, dth, dph, c.dlnP * c.dt, c.dt);
+    }
     x.boundaries(q.r_in);
     L.k += 1u;
 
@@ -69,6 +88,13 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
     else if (L.k >= L.max_steps) status = COSMICA_PATH_STEP_LIMIT;
     if (status == COSMICA_PATH_RUNNING) return false;
     x.write(a.out, L.g);
+    if constexpr (EN) {
+        const double T = en.T64();
+        a.out.lnP[L.g] = log((double)en.aoz * sqrt(T * (T + 2.0 * (double)en.m0)));
+        if (a.out.lw) a.out.lw[L.g] = en.lw();
+    } else {
+        if (a.out.lw) a.out.lw[L.g] = 0.0;
+    }
     a.out.steps[L.g] = L.k;
     a.out.status[L.g] = (uint8_t)status;
     a.out.item[L.g] = L.item;
@@ -79,12 +105,12 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
 // Persistent propagation.
 // Phase 1: lanes take particles from the device queue (one atomic per warp for all
 // lanes needing work), step them, write the exit record and refill, until the queue
-// is drained.  Phase 2 (COMPACT): the block advances in epochs of `period` steps;
-// at each checkpoint the active particles are counted and, if they occupy more
-// warps than they need, repacked through shared memory into the block's lowest
-// lanes, so that issued warp instructions keep carrying full lanes while the
-// long tail of exit times plays out.
-template <int ACC, bool COMPACT>
+// is drained.  Phase 2 (COMPACT): every `period` steps the block meets at a
+// checkpoint; the active particles are counted and, if they occupy more warps than
+// they need, repacked through shared memory into the block's lowest lanes, so that
+// issued warp instructions keep carrying full lanes while the long tail of exit
+// times plays out.  Both phases share one step site (one copy of the step code).
+template <int ACC, bool COMPACT, bool EN>
 __global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a, uint32_t period)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -94,85 +120,86 @@ __global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a, uint32_t 
     const unsigned warp = threadIdx.x >> 5;
     Lane L;
     Acc<ACC> x;
-    bool active = false, drained = false;
+    EnergyAcc<ACC, EN> en;
+    bool active = false, drained = false, phase2 = false;
     unsigned long long my_steps = 0;
-    uint32_t since_check = 0;
+    uint32_t tick = 0;   // phase 1: steps since the last drained check; phase 2: steps since the checkpoint
 
-    // ---- phase 1: queue-fed
     while (true) {
-        const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
-        if (need) {
-            unsigned long long base = 0;
-            const unsigned leader = __ffs(need) - 1;
-            if (lane == leader) base = atomicAdd(a.cursor, (unsigned long long)__popc(need));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (need & (1u << lane)) {
-                const uint64_t q = base + __popc(need & ((1u << lane) - 1u));
-                if (q < a.n_total) {
-                    start_particle<ACC>(a, q, L, x);
-                    active = true;
-                } else {
-                    drained = true;
+        if (!phase2) {
+            const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
+            if (need) {
+                unsigned long long base = 0;
+                const unsigned leader = __ffs(need) - 1;
+                if (lane == leader) base = atomicAdd(a.cursor, (unsigned long long)__popc(need));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (need & (1u << lane)) {
+                    const uint64_t q = base + __popc(need & ((1u << lane) - 1u));
+                    if (q < a.n_total) {
+                        start_particle<ACC, EN>(a, q, L, x, en);
+                        active = true;
+                    } else {
+                        drained = true;
+                    }
                 }
             }
-        }
-        if (COMPACT) {
-            // learn of the drained queue even when no lane of the warp needed work
-            if (++since_check >= period) {
-                since_check = 0;
-                unsigned dq = 0;
-                if (lane == 0) dq = *(volatile unsigned long long *)a.cursor >= a.n_total;
-                if (__shfl_sync(0xffffffffu, dq, 0)) drained = true;
-            }
-            if (__all_sync(0xffffffffu, drained || active) && __any_sync(0xffffffffu, drained)) {
-                drained = true;
+            if (COMPACT) {
+                // learn of the drained queue even when no lane of the warp needed work
+                if (++tick >= period) {
+                    tick = 0;
+                    unsigned dq = 0;
+                    if (lane == 0) dq = *(volatile unsigned long long *)a.cursor >= a.n_total;
+                    if (__shfl_sync(0xffffffffu, dq, 0)) drained = true;
+                }
+                if (__all_sync(0xffffffffu, drained || active) && __any_sync(0xffffffffu, drained)) {
+                    drained = true;
+                    phase2 = true;
+                    tick = 0;
+                }
+            } else if (!__any_sync(0xffffffffu, active)) {
                 break;
             }
-        } else if (!__any_sync(0xffffffffu, active)) {
-            break;
         }
-        if (active && step<ACC>(a, L, x, my_steps)) active = false;
-    }
-
-    if (COMPACT) {
-        // ---- phase 2: epochs with block compaction
-        Packed<ACC> *pack = reinterpret_cast<Packed<ACC> *>(smem_raw);
-        const unsigned nwarps = blockDim.x >> 5;
-        while (true) {
-            if (threadIdx.x == 0) s_count = 0;
-            __syncthreads();
-            const unsigned bal = __ballot_sync(0xffffffffu, active);
-            if (lane == 0) {
-                s_warp[warp] = __popc(bal);
-                atomicAdd(&s_count, (unsigned)__popc(bal));
-            }
-            __syncthreads();
-            const unsigned n = s_count;
-            if (n == 0) break;
-            unsigned occupied = 0, before = 0;
-            for (unsigned w = 0; w < nwarps; ++w) {
-                occupied += s_warp[w] > 0;
-                if (w < warp) before += s_warp[w];
-            }
-            if (occupied > (n + 31) / 32) {
-                if (active) {
-                    const unsigned rank = before + __popc(bal & ((1u << lane) - 1u));
-                    pack[rank].L = L;
-                    pack[rank].x = x;
+        if (COMPACT && phase2) {
+            if (tick == 0) {
+                // checkpoint: every warp of the block arrives here once per epoch
+                if (threadIdx.x == 0) s_count = 0;
+                __syncthreads();
+                const unsigned bal = __ballot_sync(0xffffffffu, active);
+                if (lane == 0) {
+                    s_warp[warp] = __popc(bal);
+                    atomicAdd(&s_count, (unsigned)__popc(bal));
                 }
                 __syncthreads();
-                active = threadIdx.x < n;
-                if (active) {
-                    L = pack[threadIdx.x].L;
-                    x = pack[threadIdx.x].x;
+                const unsigned n = s_count;
+                if (n == 0) break;
+                unsigned occupied = 0, before = 0;
+                for (unsigned w = 0; w < (blockDim.x >> 5); ++w) {
+                    occupied += s_warp[w] > 0;
+                    if (w < warp) before += s_warp[w];
                 }
+                if (occupied > (n + 31) / 32) {
+                    Packed<ACC, EN> *pack = reinterpret_cast<Packed<ACC, EN> *>(smem_raw);
+                    if (active) {
+                        const unsigned rank = before + __popc(bal & ((1u << lane) - 1u));
+                        pack[rank].L = L;
+                        pack[rank].x = x;
+                        pack[rank].en = en;
+                    }
+                    __syncthreads();
+                    active = threadIdx.x < n;
+                    if (active) {
+                        L = pack[threadIdx.x].L;
+                        x = pack[threadIdx.x].x;
+                        en = pack[threadIdx.x].en;
+                    }
+                }
+                __syncthreads();
             }
-            __syncthreads();
-            for (uint32_t it = 0; it < period; ++it) {
-                if (!__any_sync(0xffffffffu, active)) break;
-                if (active && step<ACC>(a, L, x, my_steps)) active = false;
-            }
+            // an idle warp goes straight to the next checkpoint
+            tick = __any_sync(0xffffffffu, active) ? (tick + 1 == period ? 0 : tick + 1) : 0;
         }
+        if (active && step<ACC, EN>(a, L, x, en, my_steps)) active = false;
     }
     if (a.steps_total) {
         for (int o = 16; o > 0; o >>= 1) my_steps += __shfl_down_sync(0xffffffffu, my_steps, o);
@@ -195,38 +222,46 @@ __global__ void k_debug_eval32(const DevParams *__restrict__ prm, const DevSpeci
 
 }  // namespace
 
-template <int ACC>
-static size_t pack_bytes(unsigned block) { return (size_t)block * sizeof(Packed<ACC>); }
+template <int ACC, bool EN>
+static size_t pack_bytes(unsigned block) { return (size_t)block * sizeof(Packed<ACC, EN>); }
 
-int mixed_max_blocks_per_sm(int acc, unsigned block)
+template <int ACC, bool COMPACT>
+static int occupancy(unsigned block)
 {
     int nb = 0;
-    if (acc == COSMICA_PREC_MIXED_F64ACC)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<COSMICA_PREC_MIXED_F64ACC, true>,
-                                                      (int)block, pack_bytes<COSMICA_PREC_MIXED_F64ACC>(block));
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<COSMICA_PREC_MIXED, true>, (int)block,
-                                                      pack_bytes<COSMICA_PREC_MIXED>(block));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<ACC, COMPACT, false>, (int)block,
+                                                  COMPACT ? pack_bytes<ACC, false>(block) : 0);
     return nb;
 }
 
-cudaError_t launch_propagate_mixed(const LaunchArgs &a, int acc, PersistentShape shape, cudaStream_t s)
+int mixed_max_blocks_per_sm(int acc, unsigned block, bool compact)
+{
+    if (acc == COSMICA_PREC_MIXED_F64ACC)
+        return compact ? occupancy<COSMICA_PREC_MIXED_F64ACC, true>(block)
+                       : occupancy<COSMICA_PREC_MIXED_F64ACC, false>(block);
+    return compact ? occupancy<COSMICA_PREC_MIXED, true>(block) : occupancy<COSMICA_PREC_MIXED, false>(block);
+}
+
+template <int ACC, bool EN>
+static void launch_variant(const LaunchArgs &a, PersistentShape shape, cudaStream_t s)
+{
+    const uint32_t per = shape.compact_period;
+    if (per)
+        k_propagate_mixed<ACC, true, EN><<<shape.grid, shape.block, pack_bytes<ACC, EN>(shape.block), s>>>(a, per);
+    else
+        k_propagate_mixed<ACC, false, EN><<<shape.grid, shape.block, 0, s>>>(a, 1);
+}
+
+cudaError_t launch_propagate_mixed(const LaunchArgs &a, int acc, bool energy, PersistentShape shape, cudaStream_t s)
 {
     if (a.n_total == 0) return cudaSuccess;
     cudaGetLastError();
-    const uint32_t per = shape.compact_period;
     if (acc == COSMICA_PREC_MIXED_F64ACC) {
-        if (per)
-            k_propagate_mixed<COSMICA_PREC_MIXED_F64ACC, true>
-                <<<shape.grid, shape.block, pack_bytes<COSMICA_PREC_MIXED_F64ACC>(shape.block), s>>>(a, per);
-        else
-            k_propagate_mixed<COSMICA_PREC_MIXED_F64ACC, false><<<shape.grid, shape.block, 0, s>>>(a, 1);
+        if (energy) launch_variant<COSMICA_PREC_MIXED_F64ACC, true>(a, shape, s);
+        else launch_variant<COSMICA_PREC_MIXED_F64ACC, false>(a, shape, s);
     } else {
-        if (per)
-            k_propagate_mixed<COSMICA_PREC_MIXED, true>
-                <<<shape.grid, shape.block, pack_bytes<COSMICA_PREC_MIXED>(shape.block), s>>>(a, per);
-        else
-            k_propagate_mixed<COSMICA_PREC_MIXED, false><<<shape.grid, shape.block, 0, s>>>(a, 1);
+        if (energy) launch_variant<COSMICA_PREC_MIXED, true>(a, shape, s);
+        else launch_variant<COSMICA_PREC_MIXED, false>(a, shape, s);
     }
     note_launch();
     return cudaGetLastError();

@@ -107,6 +107,7 @@ extern "C" cosmica_status cosmica_propagate_noalloc(const cosmica_params *params
     if (!out->r || !out->th || !out->ph || !out->lnP || !out->s || !out->steps || !out->status || !out->item)
         return fail(COSMICA_ERR_INVALID, "exit-state arrays must be non-NULL");
     if (!is_device_ptr(out->r)) return fail(COSMICA_ERR_INVALID, "cosmica_propagate_noalloc needs device exit states");
+    if (params->formulation == 1 && !out->lw) return fail(COSMICA_ERR_INVALID, "the energy form needs out->lw");
 
     unsigned char *base = nullptr;
     st = scratch_address(&base);
@@ -131,16 +132,17 @@ extern "C" cosmica_status cosmica_propagate_noalloc(const cosmica_params *params
     if (e != cudaSuccess) return cuda_fail(e, "cosmica_propagate_noalloc set-up");
 
     LaunchArgs a{d_prm, d_spc, d_items, d_prefix, n_energies, total,
-                 ExitPtrs{out->r, out->th, out->ph, out->lnP, out->s, out->steps, out->status, out->item},
+                 ExitPtrs{out->r, out->th, out->ph, out->lnP, out->s, out->steps, out->status, out->item, out->lw},
                  d_counters + 1, d_counters, nullptr, d_prefix};
     if (params->precision == COSMICA_PREC_FP64) {
         e = launch_propagate_fp64(a, s);
     } else {
         const unsigned block = 128;
-        const int bps = std::max(1, mixed_max_blocks_per_sm(params->precision, block));
+        const int bps = std::max(1, mixed_max_blocks_per_sm(params->precision, block, true));
         uint64_t grid = (uint64_t)num_sms() * (uint64_t)bps;
         grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (total + block - 1) / block));
-        e = launch_propagate_mixed(a, params->precision, PersistentShape{block, (unsigned)grid, 64u}, s);
+        e = launch_propagate_mixed(a, params->precision, params->formulation == 1,
+                                   PersistentShape{block, (unsigned)grid, 64u}, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "cosmica_propagate_noalloc launch");
     return COSMICA_OK;

@@ -5,9 +5,11 @@
 //   k_histogram  one thread per exit state; lanes of a warp that fall in the
 //                same (item, bin) are merged with __match_any_sync and add
 //                their count with one 64-bit atomic (integer, deterministic)
-//   k_spectrum   one block per item: J = (P0^2/beta0) (1/N) sum_b c_b w_b,
-//                w_b = J_LIS(T_b) beta_b / P_b^2 at the bin's log-centre, and
-//                sigma = std of the summand / sqrt(N); fixed-order reductions
+//   k_spectrum   one block per item: J = P0^2 (1/N) sum_b c_b w_b,
+//                w_b = J_LIS(T_b) / P_b^2 at the bin's log-centre (J = f P^2 is
+//                the intensity per unit kinetic energy and f is conserved along
+//                a path), and sigma = std of the summand / sqrt(N); fixed-order
+//                reductions
 #include <cstdint>
 
 #include "common.cuh"
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_spectrum(const unsigned long l
     const SpecItem it = items[e];
     const unsigned long long *h = hist + (size_t)e * (nbins + 3u) + 1u;
     const double zoa = fabs(it.Z) / it.A;
-    // bin weight w_b = J_LIS(T_b) beta_b / P_b^2
+    // bin weight w_b = J_LIS(T_b) / P_b^2
     double cnt = 0.0, s1 = 0.0;
     for (uint32_t b = threadIdx.x; b < nbins; b += kSpecThreads) {
         const double c = (double)h[b];
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_spectrum(const unsigned long l
         const double pn = Pb * zoa;
         const double En = sqrt(pn * pn + it.m0 * it.m0);
         const double Tb = pn * pn / (En + it.m0);
-        const double w = lis_value(lis_kind, Tb, lnT, lnJ, lis_n) * (pn / En) / (Pb * Pb);
+        const double w = lis_value(lis_kind, Tb, lnT, lnJ, lis_n) / (Pb * Pb);
         cnt += c;
         s1 += c * w;
     }
@@ -111,16 +113,14 @@ __global__ void __launch_bounds__(kSpecThreads) k_spectrum(const unsigned long l
         const double pn = Pb * zoa;
         const double En = sqrt(pn * pn + it.m0 * it.m0);
         const double Tb = pn * pn / (En + it.m0);
-        const double w = lis_value(lis_kind, Tb, lnT, lnJ, lis_n) * (pn / En) / (Pb * Pb);
+        const double w = lis_value(lis_kind, Tb, lnT, lnJ, lis_n) / (Pb * Pb);
         s2 += c * (w - mu) * (w - mu);
     }
     const double S2 = block_sum<kSpecThreads>(s2, sh);
     if (threadIdx.x == 0) {
         const double T0 = it.T;
         const double P0 = it.A / fabs(it.Z) * sqrt(T0 * (T0 + 2.0 * it.m0));
-        const double pn0 = P0 * zoa;
-        const double b0 = pn0 / sqrt(pn0 * pn0 + it.m0 * it.m0);
-        const double pref = P0 * P0 / b0;
+        const double pref = P0 * P0;
         if (N == 0.0) {
             J[e] = __longlong_as_double(0x7FF8000000000000ll);
             sigma[e] = __longlong_as_double(0x7FF8000000000000ll);
@@ -131,7 +131,74 @@ __global__ void __launch_bounds__(kSpecThreads) k_spectrum(const unsigned long l
     }
 }
 
+// Unbinned Eq. 4 over the contiguous exit states of one item per block:
+//   momentum form: summand P0^2 J_LIS(T_ex) / P_ex^2
+//   energy form:   summand beta0 J_LIS(T_ex) exp(lw) / beta_ex  (lw = -sum L ds)
+__device__ double unbinned_summand(const SpecItem &it, int form, double lnP, double lw, int lis_kind,
+                                   const double *lnT, const double *lnJ, uint32_t lis_n)
+{
+    const double zoa = fabs(it.Z) / it.A;
+    const double P = exp(lnP);
+    const double pn = P * zoa;
+    const double En = sqrt(pn * pn + it.m0 * it.m0);
+    const double T = pn * pn / (En + it.m0);
+    const double J = lis_value(lis_kind, T, lnT, lnJ, lis_n);
+    const double T0 = it.T;
+    const double P0 = it.A / fabs(it.Z) * sqrt(T0 * (T0 + 2.0 * it.m0));
+    if (form == 0) return P0 * P0 * J / (P * P);
+    const double pn0 = P0 * zoa;
+    const double b0 = pn0 / sqrt(pn0 * pn0 + it.m0 * it.m0);
+    return b0 * J * exp(lw) / (pn / En);
+}
+
+__global__ void __launch_bounds__(kSpecThreads) k_spectrum_unbinned(ExitPtrs ex, const uint64_t *__restrict__ prefix,
+                                                                    const SpecItem *__restrict__ items, int form,
+                                                                    int lis_kind, const double *lnT, const double *lnJ,
+                                                                    uint32_t lis_n, double *J, double *sigma)
+{
+    __shared__ double sh[kSpecThreads];
+    const uint32_t e = blockIdx.x;
+    const SpecItem it = items[e];
+    const uint64_t lo = prefix[e], hi = prefix[e + 1];
+    double cnt = 0.0, s1 = 0.0;
+    for (uint64_t g = lo + threadIdx.x; g < hi; g += kSpecThreads) {
+        if (ex.status[g] != COSMICA_PATH_EXIT) continue;
+        s1 += unbinned_summand(it, form, ex.lnP[g], ex.lw ? ex.lw[g] : 0.0, lis_kind, lnT, lnJ, lis_n);
+        cnt += 1.0;
+    }
+    const double N = block_sum<kSpecThreads>(cnt, sh);
+    const double mu = block_sum<kSpecThreads>(s1, sh) / N;
+    double s2 = 0.0;
+    for (uint64_t g = lo + threadIdx.x; g < hi; g += kSpecThreads) {
+        if (ex.status[g] != COSMICA_PATH_EXIT) continue;
+        const double d = unbinned_summand(it, form, ex.lnP[g], ex.lw ? ex.lw[g] : 0.0, lis_kind, lnT, lnJ, lis_n) - mu;
+        s2 += d * d;
+    }
+    const double S2 = block_sum<kSpecThreads>(s2, sh);
+    if (threadIdx.x == 0) {
+        if (N == 0.0) {
+            J[e] = __longlong_as_double(0x7FF8000000000000ll);
+            sigma[e] = __longlong_as_double(0x7FF8000000000000ll);
+        } else {
+            J[e] = mu;
+            sigma[e] = (N > 1.0) ? sqrt(S2 / (N - 1.0) / N) : 0.0;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_spectrum_unbinned(const ExitPtrs &ex, const uint64_t *prefix, uint32_t n_items,
+                                     const SpecItem *items, int form, int lis_kind, const double *lis_lnT,
+                                     const double *lis_lnJ, uint32_t lis_n, double *J, double *sigma, cudaStream_t s)
+{
+    if (n_items == 0) return cudaSuccess;
+    cudaGetLastError();
+    k_spectrum_unbinned<<<n_items, kSpecThreads, 0, s>>>(ex, prefix, items, form, lis_kind, lis_lnT, lis_lnJ, lis_n,
+                                                         J, sigma);
+    note_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_histogram(const ExitPtrs &ex, uint64_t n, uint32_t n_items, uint32_t nbins, double x_lo,
                              double dx, unsigned long long *hist, cudaStream_t s)

@@ -120,11 +120,47 @@ struct Acc<COSMICA_PREC_MIXED_F64ACC> {
 };
 
 
+// Energy form (Eq. 1): kinetic energy per nucleon T and the loss integral
+// Lam = sum L ds of Eq. 4, accumulated with the same precision as the state.
+// The momentum form carries nothing.
+template <int ACC, bool EN>
+struct EnergyAcc {
+    __device__ void init(double, float, float) {}
+};
+
+template <>
+struct EnergyAcc<COSMICA_PREC_MIXED, true> {
+    m32::FF T, Lam;
+    float m0, aoz;
+    __device__ void init(double T0, float m0_, float aoz_)
+    {
+        T = m32::ff_from_double(T0);
+        Lam.hi = 0.0f; Lam.lo = 0.0f;
+        m0 = m0_; aoz = aoz_;
+    }
+    __device__ float fT() const { return T.hi; }
+    __device__ void add(float dT, float dLam) { m32::ff_add(T, dT); m32::ff_add(Lam, dLam); }
+    __device__ double T64() const { return m32::ff_to_double(T); }
+    __device__ double lw() const { return -m32::ff_to_double(Lam); }
+};
+
+template <>
+struct EnergyAcc<COSMICA_PREC_MIXED_F64ACC, true> {
+    double T, Lam;
+    float m0, aoz;
+    __device__ void init(double T0, float m0_, float aoz_) { T = T0; Lam = 0.0; m0 = m0_; aoz = aoz_; }
+    __device__ float fT() const { return (float)T; }
+    __device__ void add(float dT, float dLam) { T += (double)dT; Lam += (double)dLam; }
+    __device__ double T64() const { return T; }
+    __device__ double lw() const { return -Lam; }
+};
+
 // a lane's complete state, moved through shared memory by block compaction
-template <int ACC>
+template <int ACC, bool EN>
 struct Packed {
     Lane L;
     Acc<ACC> x;
+    EnergyAcc<ACC, EN> en;
 };
 
 }  // namespace cosmica

@@ -46,6 +46,7 @@ struct Drift {
     float l00, l11, l20, l22;
     float inv_r, inv_rs;
     float dlnP, dt;
+    float beta;        // speed / c at the start of the step
 };
 
 // Coefficients at (r, th, ph, lnP).  q: FP32 constants of the heliosphere.
@@ -55,6 +56,7 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
 {
     const float P = __expf(lnP);
     const float beta = P * rsqrtf(fmaf(P, P, M2));
+    o.beta = beta;
     float sn, cs;
     __sincosf(th, &sn, &cs);
     const float inv_sn = __fdividef(1.0f, sn);

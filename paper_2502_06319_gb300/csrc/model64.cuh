@@ -270,6 +270,7 @@ __device__ __forceinline__ void normals(uint64_t seed, uint64_t pid, uint32_t k,
 
 struct State {
     double r, th, ph, lnP, s;
+    double T, Lam, r_old;      // energy form: kinetic energy per nucleon, loss integral
     uint32_t k;
     int status;
 };
@@ -280,6 +281,7 @@ __device__ __forceinline__ void em_step(const DevParams &p, const DevSpecies &sp
                                         uint64_t pid, State &x)
 {
     double z[3];
+    x.r_old = x.r;
     normals(seed, pid, x.k, z);
     Coef c;
     eval(p, sp, x.r, x.th, x.ph, x.lnP, c);
@@ -297,7 +299,17 @@ __device__ __forceinline__ void em_step(const DevParams &p, const DevSpecies &sp
     x.r = x.r + dr;
     x.th = x.th + dth;
     x.ph = x.ph + dph;
-    x.lnP = x.lnP + dlnP;
+    if (p.formulation != 0.0) {
+        // Eq. 1 backward: A_T = (2/3)(V/r) alpha T, loss L = (2V/(3r)) (1 + beta^2)
+        const double alpha = (x.T + 2.0 * sp.m0) / (x.T + sp.m0);
+        const double A_T = 2.0 * c.V / (3.0 * x.r_old) * alpha * x.T;
+        const double Lloss = 2.0 * c.V / (3.0 * x.r_old) * (1.0 + c.beta * c.beta);
+        x.T = x.T + A_T * dt;
+        x.Lam = x.Lam + Lloss * dt;
+        x.lnP = dm::log(sp.A / fabs(sp.Z) * sqrt(x.T * (x.T + 2.0 * sp.m0)));
+    } else {
+        x.lnP = x.lnP + dlnP;
+    }
     if (x.r < p.r_in) x.r = 2.0 * p.r_in - x.r;
     {
         const double t = x.th - kTwoPi * floor(x.th / kTwoPi);
@@ -325,6 +337,8 @@ __device__ __forceinline__ void init_state(const DevParams &p, const DevSpecies 
     x.r = p.r0; x.th = p.th0; x.ph = p.ph0;
     const double P0 = sp.A / fabs(sp.Z) * sqrt(T * (T + 2.0 * sp.m0));
     x.lnP = dm::log(P0);
+    x.T = T;
+    x.Lam = 0.0;
     x.s = 0.0;
     x.k = 0u;
     x.status = COSMICA_PATH_RUNNING;

@@ -32,7 +32,7 @@ PARAM_FIELDS = (
     "lat_fast_deg", "tilt_deg", "polarity", "drift_on", "hcs_on", "R_out", "R_ts",
     "ts_K_factor", "r_in", "dt_max", "dt_fixed", "max_steps", "isotropic",
     "V_const_kms", "eps_adv", "eps_diff", "dt_min", "dlat_deg", "dts_AU",
-    "dcs_min_deg", "rot_period_day", "r0", "th0", "ph0",
+    "dcs_min_deg", "rot_period_day", "r0", "th0", "ph0", "formulation",
 )
 
 DEFAULT_PARAMS: Dict[str, float] = {
@@ -66,6 +66,7 @@ DEFAULT_PARAMS: Dict[str, float] = {
     "r0": 1.0,
     "th0": math.pi / 2.0,
     "ph0": 0.0,
+    "formulation": 0.0,     # 0: momentum form (Eq. 5-6); 1: energy form with loss weight (Eq. 1, Eq. 4)
 }
 
 

@@ -9,12 +9,13 @@ def torch():
     return t
 
 
-def gpu_run(job, precision=cz.PREC_FP64, host_out=False, params=None):
+def gpu_run(job, precision=cz.PREC_FP64, host_out=False, params=None, with_lw=False):
     """Propagate a workload with cosmica_propagate; returns (numpy dict, ExitBuffers, model)."""
     t = torch()
     m = cz.Model(cz.make_params(params or job.params, precision))
     sp = cz.make_species(job.species)
-    out = cz.ExitBuffers(job.n_particles, device="cpu" if host_out else "cuda", pin_memory=host_out)
+    out = cz.ExitBuffers(job.n_particles, device="cpu" if host_out else "cuda", pin_memory=host_out,
+                         with_lw=with_lw)
     cz.cosmica_propagate(m.h, sp, job.T_in, job.n_per_energy, job.seed, out)
     t.cuda.synchronize()
     return out.numpy(), out, m
@@ -44,3 +45,13 @@ def compare_paths(g, o, rel=1e-10):
                 d = np.minimum(d, np.abs(np.abs(a - b) - 2 * np.pi) / np.maximum(np.abs(b), 1e-300))
             worst = max(worst, float(d.max()))
     return float(same.mean()), worst
+
+
+def gpu_unbinned(job, out, formulation):
+    t = torch()
+    nE = len(job.T_in)
+    J = t.empty(nE, dtype=t.float64, device="cuda")
+    S = t.empty(nE, dtype=t.float64, device="cuda")
+    cz.cosmica_spectrum_unbinned(out, cz.make_species(job.species), job.T_in, job.n_per_energy, formulation, J, S)
+    t.cuda.synchronize()
+    return J.cpu().numpy(), S.cpu().numpy()

@@ -179,9 +179,8 @@ def test_histogram_and_binned_estimator_by_brute_force(orc):
             Pc = math.sqrt(edges[b] * edges[b + 1])
             pn = Pc
             Tc = math.sqrt(pn * pn + W.PROTON["m0"] ** 2) - W.PROTON["m0"]
-            bc = pn / math.sqrt(pn * pn + W.PROTON["m0"] ** 2)
-            vals += [orc.lis(Tc) * bc / Pc ** 2] * int(H[e, 1 + b])
+            vals += [orc.lis(Tc) / Pc ** 2] * int(H[e, 1 + b])
         P0 = math.sqrt(T0[e] * (T0[e] + 2 * W.PROTON["m0"]))
-        pref = P0 ** 2 / (P0 / math.sqrt(P0 * P0 + W.PROTON["m0"] ** 2))
+        pref = P0 ** 2
         assert math.isclose(J[e], pref * np.mean(vals), rel_tol=1e-9)
         assert math.isclose(S[e], pref * np.std(vals, ddof=1) / math.sqrt(len(vals)), rel_tol=1e-9)
