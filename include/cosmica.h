@@ -204,6 +204,37 @@ cosmica_status cosmica_propagate(cosmica_model *model, const cosmica_species *sp
                                  const uint32_t *n_per_energy, uint64_t seed,
                                  cosmica_exit_states *out, void *stream);
 
+/* One detection point of an orbit (Sec. IV.A: the detection point may move
+ * along a spacecraft orbit; the quasi-particle sample is subdivided among the
+ * positions, which integrates the flux over the orbit and the mission time). */
+typedef struct {
+    double r_AU;      /* heliocentric radius, r_in <= r < R_out                  */
+    double th_rad;    /* colatitude, in (0, pi)                                   */
+    double ph_rad;    /* longitude (any finite value; kept modulo 2 pi)           */
+    double weight;    /* share of the sample (e.g. time spent there), > 0         */
+} cosmica_position;
+
+/*
+ * cosmica_propagate with the start point moving along an orbit.  The
+ * n_per_energy[e] quasi-particles of energy e are split among the positions in
+ * proportion to their weights, in position order and contiguously: with
+ * W_m = weight[0] + ... + weight[m-1] (summed in this order, W = W_n_positions),
+ * position m receives the particles i of energy e with
+ *   c_m <= i < c_(m+1),  c_m = floor(n_e * W_m / W)  (FP64, c_n_positions = n_e).
+ * Particle identities are those of cosmica_propagate (pid = sum_{e'<e} n_e' + i),
+ * exit entry g belongs to the same particle as there, and out->item receives
+ * the energy index, so cosmica_spectrum and cosmica_spectrum_unbinned return the
+ * orbit-averaged spectrum unchanged.  A single position equal to the parameter
+ * set's (r0, th0, ph0) reproduces cosmica_propagate bit for bit.
+ *   positions      host [n_positions], n_positions >= 1
+ * Errors: INVALID (sizes, null pointers, a position outside the heliosphere or
+ * a weight <= 0), OOM, CUDA. */
+cosmica_status cosmica_propagate_orbit(cosmica_model *model, const cosmica_species *species,
+                                       const double *T_in_GeVn, uint32_t n_energies,
+                                       const uint32_t *n_per_energy, const cosmica_position *positions,
+                                       uint32_t n_positions, uint64_t seed, cosmica_exit_states *out,
+                                       void *stream);
+
 /*
  * Propagation that allocates nothing.  The paper has no counterpart: this is
  * an interface for callers that cannot allocate device memory -- code running
@@ -215,7 +246,7 @@ cosmica_status cosmica_propagate(cosmica_model *model, const cosmica_species *sp
  * Same arguments and results as cosmica_propagate, with the parameter set
  * passed directly instead of a model handle.  The library's scratch for the
  * call (parameter block, species, work items, prefix sums, queue cursor,
- * step counter) is a fixed static device array of about 45 KB that every GPU
+ * step counter) is a fixed static device array of about 75 KB that every GPU
  * loading the library holds until the process exits; the call makes no
  * cudaMalloc, cudaFree or other allocating call.
  *   n_energies   at most COSMICA_NOALLOC_MAX_ENERGIES (INVALID otherwise)
@@ -279,6 +310,9 @@ typedef struct {
     uint32_t reserved;
     uint64_t first_pid;
     uint64_t seed;
+    double r0_AU;             /* start position of the item's particles (a detection  */
+    double th0_rad;           /* point of an orbit); r0_AU = 0 selects the parameter  */
+    double ph0_rad;           /* set's r0, th0, ph0                                   */
 } cosmica_work_item;
 
 /* Launch shape and scheduling of the persistent kernel.  Passing NULL selects

@@ -729,20 +729,23 @@ static double rigidity(const orc_species *sp, double T)
     return sp->A / fabs(sp->Z) * sqrt(T * (T + 2.0 * sp->m0));
 }
 
-static void init_state(const orc_params *p, const orc_species *sp, double T_in, orc_state *x)
+static void init_state(const orc_species *sp, double T_in, double r0, double th0, double ph0, orc_state *x)
 {
-    x->r = p->r0; x->th = p->th0; x->ph = p->ph0;
+    x->r = r0; x->th = th0; x->ph = ph0;
     x->lnP = orc_log(rigidity(sp, T_in));
     x->T = T_in; x->Lam = 0.0;
     x->s = 0.0; x->k = 0u; x->status = ORC_RUNNING;
 }
 
 /* Propagate n quasi-particles; particle i uses parameter set prm_idx[i],
- * species sp_idx[i], initial energy T_in[i], identity pid[i], key seed[i].
- * Each particle is independent, so any thread count gives the same result. */
+ * species sp_idx[i], initial energy T_in[i], identity pid[i], key seed[i] and
+ * starts at start[3i .. 3i+2] = (r0, th0, ph0) (a point of the detector's
+ * orbit, Sec. IV.A), or at the parameter set's (r0, th0, ph0) when start is
+ * NULL.  Each particle is independent, so any thread count gives the same
+ * result. */
 void orc_run_particles(const orc_params *prm, const orc_species *spc, uint64_t n,
                        const uint32_t *prm_idx, const uint32_t *sp_idx, const double *T_in,
-                       const uint64_t *pid, const uint64_t *seed,
+                       const uint64_t *pid, const uint64_t *seed, const double *start,
                        double *r, double *th, double *ph, double *lnP, double *s,
                        uint32_t *steps, uint8_t *status, double *lw, int nthreads)
 {
@@ -754,7 +757,10 @@ void orc_run_particles(const orc_params *prm, const orc_species *spc, uint64_t n
         const orc_params *p = prm + prm_idx[i];
         const orc_species *sp = spc + sp_idx[i];
         orc_state x;
-        init_state(p, sp, T_in[i], &x);
+        if (start)
+            init_state(sp, T_in[i], start[3 * i], start[3 * i + 1], start[3 * i + 2], &x);
+        else
+            init_state(sp, T_in[i], p->r0, p->th0, p->ph0, &x);
         while (x.status == ORC_RUNNING) em_step(p, sp, seed[i], pid[i], &x, 0);
         r[i] = x.r; th[i] = x.th; ph[i] = x.ph; lnP[i] = x.lnP; s[i] = x.s;
         steps[i] = x.k; status[i] = (uint8_t)x.status;
@@ -767,7 +773,7 @@ int orc_trace(const orc_params *p, const orc_species *sp, double T_in, uint64_t 
               uint32_t nsteps, double *out)
 {
     orc_state x;
-    init_state(p, sp, T_in, &x);
+    init_state(sp, T_in, p->r0, p->th0, p->ph0, &x);
     uint32_t i = 0;
     for (; i < nsteps && x.status == ORC_RUNNING; ++i) {
         double dt;

@@ -92,7 +92,7 @@ def lib():
                                    C.c_double, C.c_double, C.c_double, C.c_double, f64p]
             L.orc_eval_n.restype = C.c_int
             L.orc_run_particles.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcSpecies), C.c_uint64,
-                                            u32p, u32p, f64p, u64p, u64p,
+                                            u32p, u32p, f64p, u64p, u64p, C.c_void_p,
                                             f64p, f64p, f64p, f64p, f64p, u32p, u8p, f64p, C.c_int]
             L.orc_trace.argtypes = [C.POINTER(OrcParams), C.POINTER(OrcSpecies), C.c_double,
                                     C.c_uint64, C.c_uint64, C.c_uint32, f64p]
@@ -165,20 +165,49 @@ def expand(n_per_energy, first_pid: int = 0):
     return e, pid
 
 
+def orbit_starts(n_per_energy, positions) -> np.ndarray:
+    """Moving detection point (Sec. IV.A): the sample of every energy is divided among the
+    orbit's positions (r, th, ph, weight) in proportion to the weights, in position order and
+    in contiguous runs: with W_m the sum of the weights before position m and W their total,
+    position m takes the particles c_m <= i < c_(m+1), c_m = floor(n W_m / W).
+    Returns the start point (r0, th0, ph0) of every particle, in particle order."""
+    rows = []
+    for n in n_per_energy:
+        n = int(n)
+        W = 0.0
+        for q in positions:
+            W += float(q[3])
+        cuts, Wm = [], 0.0
+        for q in positions:
+            cuts.append(math.floor(n * Wm / W))
+            Wm += float(q[3])
+        cuts.append(n)
+        for m, q in enumerate(positions):
+            rows += [(float(q[0]), float(q[1]), float(q[2]))] * (cuts[m + 1] - cuts[m])
+    return np.array(rows, dtype=np.float64).reshape(-1, 3)
+
+
 def run(p: dict, species: dict, T_in, n_per_energy, seed: int, select=None, threads: int = 0,
-        first_pid: int = 0) -> dict:
-    """Propagate every quasi-particle of one job (or only the global indices in `select`)."""
+        first_pid: int = 0, positions=None) -> dict:
+    """Propagate every quasi-particle of one job (or only the global indices in `select`);
+    with `positions`, the start points follow orbit_starts."""
     T_in = np.asarray(T_in, dtype=np.float64)
     e, pid = expand(n_per_energy, first_pid)
+    start = None if positions is None else orbit_starts(n_per_energy, positions)
     if select is not None:
         select = np.asarray(select, dtype=np.int64)
         e, pid = e[select], pid[select]
+        start = None if start is None else start[select]
     return run_particles([p], [species], np.zeros(len(e), np.uint32), np.zeros(len(e), np.uint32),
-                         T_in[e], pid, np.full(len(e), seed, np.uint64), threads) | {"energy": e}
+                         T_in[e], pid, np.full(len(e), seed, np.uint64), threads, start=start) | {"energy": e}
 
 
-def run_particles(param_sets, species_list, prm_idx, sp_idx, T, pid, seed, threads: int = 0) -> dict:
+def run_particles(param_sets, species_list, prm_idx, sp_idx, T, pid, seed, threads: int = 0,
+                  start=None) -> dict:
+    """start: optional (n, 3) array of per-particle start points (r0, th0, ph0)."""
     n = len(T)
+    if start is not None:
+        start = np.ascontiguousarray(start, np.float64).reshape(n, 3)
     prm = (OrcParams * max(1, len(param_sets)))(*[_params(p) for p in param_sets])
     spc = (OrcSpecies * max(1, len(species_list)))(*[_species(s) for s in species_list])
     out = {k: np.empty(n, np.float64) for k in ("r", "th", "ph", "lnP", "s")}
@@ -189,6 +218,7 @@ def run_particles(param_sets, species_list, prm_idx, sp_idx, T, pid, seed, threa
                             np.ascontiguousarray(prm_idx, np.uint32), np.ascontiguousarray(sp_idx, np.uint32),
                             np.ascontiguousarray(T, np.float64), np.ascontiguousarray(pid, np.uint64),
                             np.ascontiguousarray(seed, np.uint64),
+                            None if start is None else start.ctypes.data,
                             out["r"], out["th"], out["ph"], out["lnP"], out["s"], out["steps"],
                             out["status"], out["lw"], int(threads))
     return out

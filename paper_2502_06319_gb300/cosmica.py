@@ -63,7 +63,12 @@ class cosmica_bins(C.Structure):
 
 class cosmica_work_item(C.Structure):
     _fields_ = [("param_idx", C.c_uint32), ("species_idx", C.c_uint32), ("T_GeVn", C.c_double),
-                ("n", C.c_uint32), ("reserved", C.c_uint32), ("first_pid", C.c_uint64), ("seed", C.c_uint64)]
+                ("n", C.c_uint32), ("reserved", C.c_uint32), ("first_pid", C.c_uint64), ("seed", C.c_uint64),
+                ("r0_AU", C.c_double), ("th0_rad", C.c_double), ("ph0_rad", C.c_double)]
+
+
+class cosmica_position(C.Structure):
+    _fields_ = [("r_AU", C.c_double), ("th_rad", C.c_double), ("ph_rad", C.c_double), ("weight", C.c_double)]
 
 
 class cosmica_tuning(C.Structure):
@@ -134,6 +139,10 @@ def lib():
                                                     C.POINTER(C.c_double), C.c_uint32, C.POINTER(C.c_uint32),
                                                     C.c_uint64, C.POINTER(cosmica_exit_states), P]
             L.cosmica_propagate_noalloc.restype = C.c_int
+            L.cosmica_propagate_orbit.argtypes = [P, C.POINTER(cosmica_species), C.POINTER(C.c_double), C.c_uint32,
+                                                  C.POINTER(C.c_uint32), C.POINTER(cosmica_position), C.c_uint32,
+                                                  C.c_uint64, C.POINTER(cosmica_exit_states), P]
+            L.cosmica_propagate_orbit.restype = C.c_int
             L.cosmica_server_create.argtypes = [C.c_size_t, C.c_int32, C.c_uint32, C.POINTER(P)]
             L.cosmica_server_submit.argtypes = [P, C.POINTER(cosmica_request), C.POINTER(C.c_uint64)]
             L.cosmica_server_poll.argtypes = [P, C.c_uint64, C.POINTER(cosmica_result)]
@@ -288,6 +297,19 @@ def cosmica_propagate(model: int, species: cosmica_species, T_in: Sequence[float
     _check(lib().cosmica_propagate(model, C.byref(species), T, n, N, int(seed), C.byref(out.c), _stream(stream)))
 
 
+def cosmica_propagate_orbit(model: int, species: cosmica_species, T_in: Sequence[float],
+                            n_per_energy: Sequence[int], positions, seed: int, out: ExitBuffers,
+                            stream=None) -> None:
+    """positions: iterable of (r_AU, th_rad, ph_rad, weight)."""
+    n = len(T_in)
+    T = (C.c_double * max(1, n))(*[float(t) for t in T_in])
+    N = (C.c_uint32 * max(1, n))(*[int(x) for x in n_per_energy])
+    pos = list(positions)
+    arr = (cosmica_position * max(1, len(pos)))(*[cosmica_position(*map(float, q)) for q in pos])
+    _check(lib().cosmica_propagate_orbit(model, C.byref(species), T, n, N, arr, len(pos), int(seed),
+                                         C.byref(out.c), _stream(stream)))
+
+
 def cosmica_propagate_noalloc(params: cosmica_params, species: cosmica_species, T_in: Sequence[float],
                               n_per_energy: Sequence[int], seed: int, out: ExitBuffers, stream=None) -> None:
     """Allocation-free propagation: scratch in a fixed static device array (see cosmica.h)."""
@@ -320,11 +342,15 @@ def cosmica_spectrum_unbinned(exit: ExitBuffers, species: cosmica_species, T_in:
 
 # --------------------------------------------------------------- batch API --
 def make_items(items) -> "C.Array":
-    """items: iterable of (param_idx, species_idx, T, n, first_pid, seed)."""
+    """items: iterable of (param_idx, species_idx, T, n, first_pid, seed[, (r0, th0, ph0)]);
+    without the start position the parameter set's is used."""
     items = list(items)
     arr = (cosmica_work_item * max(1, len(items)))()
-    for i, (pi, si, T, n, fp, sd) in enumerate(items):
-        arr[i] = cosmica_work_item(int(pi), int(si), float(T), int(n), 0, int(fp), int(sd))
+    for i, it in enumerate(items):
+        pi, si, T, n, fp, sd = it[:6]
+        r0, th0, ph0 = it[6] if len(it) > 6 else (0.0, 0.0, 0.0)
+        arr[i] = cosmica_work_item(int(pi), int(si), float(T), int(n), 0, int(fp), int(sd),
+                                   float(r0), float(th0), float(ph0))
     return arr
 
 

@@ -71,6 +71,9 @@ struct DevItem {
     uint64_t first_pid;
     uint64_t seed;
     uint32_t param_idx, species_idx;
+    double r0, th0, ph0;       // start position (detection point) of the item's particles
+    uint32_t out_item;         // value written to the exit record's item field
+    uint32_t pad;
 };
 
 struct ExitPtrs {

@@ -103,6 +103,11 @@ cosmica_status check_params(const cosmica_params *p)
     return COSMICA_OK;
 }
 
+bool valid_start(const cosmica_params &p, double r0, double th0, double ph0)
+{
+    return std::isfinite(r0) && r0 >= p.r_in_AU && r0 < p.R_out_AU && th0 > 0.0 && th0 < kPi && std::isfinite(ph0);
+}
+
 cosmica_status check_species(const cosmica_species *s)
 {
     if (!s) return fail(COSMICA_ERR_INVALID, "species is NULL");
@@ -427,43 +432,25 @@ static cosmica_status upload_species(DevBuf &buf, Staging &stage, const cosmica_
     return COSMICA_OK;
 }
 
-extern "C" cosmica_status cosmica_propagate(cosmica_model *m, const cosmica_species *species,
-                                            const double *T_in, uint32_t n_energies, const uint32_t *n_per_energy,
-                                            uint64_t seed, cosmica_exit_states *out, void *stream)
+// Shared tail of cosmica_propagate and cosmica_propagate_orbit: upload the
+// species and the item table, launch the path's kernel, copy host exits back.
+static cosmica_status propagate_items(cosmica_model *m, const cosmica_species *species,
+                                      const std::vector<DevItem> &its, const std::vector<uint64_t> &pre,
+                                      cosmica_exit_states *out, cudaStream_t s)
 {
-    if (!m) return fail(COSMICA_ERR_INVALID, "model is NULL");
-    cosmica_status st = check_species(species);
-    if (st != COSMICA_OK) return st;
-    if (n_energies > 0 && (!T_in || !n_per_energy)) return fail(COSMICA_ERR_INVALID, "T_in / n_per_energy NULL");
-    if (!out) return fail(COSMICA_ERR_INVALID, "out is NULL");
-    uint64_t total = 0;
-    for (uint32_t e = 0; e < n_energies; ++e) {
-        if (!(std::isfinite(T_in[e]) && T_in[e] > 0.0)) return fail(COSMICA_ERR_INVALID, "T_in[%u] must be > 0", e);
-        total += n_per_energy[e];
-    }
+    const uint64_t total = pre.back();
     if (out->n != total) return fail(COSMICA_ERR_INVALID, "out->n = %llu, sum(n_per_energy) = %llu",
                                      (unsigned long long)out->n, (unsigned long long)total);
     if (total == 0) return COSMICA_OK;
     if (!valid_exit(out)) return fail(COSMICA_ERR_INVALID, "exit-state arrays must be non-NULL");
-    cudaStream_t s = (cudaStream_t)stream;
+    if (m->p.formulation == 1 && !out->lw) return fail(COSMICA_ERR_INVALID, "the energy form needs out->lw");
 
     DevSpecies *d_sp = nullptr;
-    st = upload_species(m->spc, m->spc_stage, species, 1, s, &d_sp);
+    cosmica_status st = upload_species(m->spc, m->spc_stage, species, 1, s, &d_sp);
     if (st != COSMICA_OK) return st;
-    std::vector<DevItem> its(n_energies);
-    std::vector<uint64_t> pre(n_energies + 1, 0);
-    for (uint32_t e = 0; e < n_energies; ++e) {
-        its[e].T = T_in[e];
-        its[e].first_pid = pre[e];
-        its[e].seed = seed;
-        its[e].param_idx = 0;
-        its[e].species_idx = 0;
-        pre[e + 1] = pre[e] + n_per_energy[e];
-    }
     st = m->tab.build(its, pre, cost_order(its, &m->p, species), s);
     if (st != COSMICA_OK) return st;
 
-    if (m->p.formulation == 1 && !out->lw) return fail(COSMICA_ERR_INVALID, "the energy form needs out->lw");
     const bool host_out = !is_device_ptr(out->r);
     ExitPtrs ex = exit_ptrs(out);
     if (host_out) {
@@ -483,6 +470,87 @@ extern "C" cosmica_status cosmica_propagate(cosmica_model *m, const cosmica_spec
     if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
     if (host_out) return ExitStage::copy_back(ex, out, s);
     return COSMICA_OK;
+}
+
+static cosmica_status check_energies(const double *T_in, uint32_t n_energies, const uint32_t *n_per_energy)
+{
+    if (n_energies > 0 && (!T_in || !n_per_energy)) return fail(COSMICA_ERR_INVALID, "T_in / n_per_energy NULL");
+    for (uint32_t e = 0; e < n_energies; ++e)
+        if (!(std::isfinite(T_in[e]) && T_in[e] > 0.0)) return fail(COSMICA_ERR_INVALID, "T_in[%u] must be > 0", e);
+    return COSMICA_OK;
+}
+
+extern "C" cosmica_status cosmica_propagate(cosmica_model *m, const cosmica_species *species,
+                                            const double *T_in, uint32_t n_energies, const uint32_t *n_per_energy,
+                                            uint64_t seed, cosmica_exit_states *out, void *stream)
+{
+    if (!m) return fail(COSMICA_ERR_INVALID, "model is NULL");
+    cosmica_status st = check_species(species);
+    if (st != COSMICA_OK) return st;
+    st = check_energies(T_in, n_energies, n_per_energy);
+    if (st != COSMICA_OK) return st;
+    if (!out) return fail(COSMICA_ERR_INVALID, "out is NULL");
+    std::vector<DevItem> its(n_energies);
+    std::vector<uint64_t> pre(n_energies + 1, 0);
+    for (uint32_t e = 0; e < n_energies; ++e) {
+        its[e] = make_item(T_in[e], pre[e], seed, 0u, 0u, m->p.r0_AU, m->p.th0_rad, m->p.ph0_rad, e);
+        pre[e + 1] = pre[e] + n_per_energy[e];
+    }
+    return propagate_items(m, species, its, pre, out, (cudaStream_t)stream);
+}
+
+// Split of n particles among positions by weight (Sec. IV.A, moving detection
+// point): position m takes [c_m, c_(m+1)), c_m = floor(n W_m / W), W_m the
+// weights summed in order.
+static void orbit_split(uint64_t n, const cosmica_position *pos, uint32_t n_pos, std::vector<uint64_t> &cut)
+{
+    double W = 0.0;
+    for (uint32_t j = 0; j < n_pos; ++j) W += pos[j].weight;
+    cut.assign(n_pos + 1, 0);
+    double Wm = 0.0;
+    for (uint32_t j = 0; j < n_pos; ++j) {
+        cut[j] = (uint64_t)std::floor((double)n * Wm / W);
+        Wm += pos[j].weight;
+    }
+    cut[n_pos] = n;
+}
+
+extern "C" cosmica_status cosmica_propagate_orbit(cosmica_model *m, const cosmica_species *species,
+                                                  const double *T_in, uint32_t n_energies,
+                                                  const uint32_t *n_per_energy, const cosmica_position *positions,
+                                                  uint32_t n_positions, uint64_t seed, cosmica_exit_states *out,
+                                                  void *stream)
+{
+    if (!m) return fail(COSMICA_ERR_INVALID, "model is NULL");
+    cosmica_status st = check_species(species);
+    if (st != COSMICA_OK) return st;
+    st = check_energies(T_in, n_energies, n_per_energy);
+    if (st != COSMICA_OK) return st;
+    if (!out) return fail(COSMICA_ERR_INVALID, "out is NULL");
+    if (n_positions == 0 || !positions) return fail(COSMICA_ERR_INVALID, "need at least one position");
+    for (uint32_t j = 0; j < n_positions; ++j) {
+        const cosmica_position &q = positions[j];
+        if (!valid_start(m->p, q.r_AU, q.th_rad, q.ph_rad))
+            return fail(COSMICA_ERR_INVALID, "position %u: need r_in <= r < R_out, th in (0, pi), finite ph", j);
+        if (!(std::isfinite(q.weight) && q.weight > 0.0))
+            return fail(COSMICA_ERR_INVALID, "position %u: weight must be > 0", j);
+    }
+    std::vector<DevItem> its;
+    std::vector<uint64_t> pre(1, 0), cut;
+    uint64_t first = 0;
+    for (uint32_t e = 0; e < n_energies; ++e) {
+        orbit_split(n_per_energy[e], positions, n_positions, cut);
+        for (uint32_t j = 0; j < n_positions; ++j) {
+            const uint64_t n = cut[j + 1] - cut[j];
+            if (n == 0) continue;
+            const cosmica_position &q = positions[j];
+            its.push_back(make_item(T_in[e], first + cut[j], seed, 0u, 0u, q.r_AU, q.th_rad, q.ph_rad, e));
+            pre.push_back(pre.back() + n);
+        }
+        first += n_per_energy[e];
+    }
+    if (its.size() > UINT32_MAX) return fail(COSMICA_ERR_INVALID, "too many (energy, position) items");
+    return propagate_items(m, species, its, pre, out, (cudaStream_t)stream);
 }
 
 // ============================================================ spectrum API ==
@@ -705,7 +773,12 @@ static cosmica_status batch_items(const cosmica_batch *b, const cosmica_work_ite
         if (w.param_idx >= b->params.size() || w.species_idx >= b->species.size())
             return fail(COSMICA_ERR_INVALID, "item %u: parameter or species index out of range", i);
         if (!(std::isfinite(w.T_GeVn) && w.T_GeVn > 0.0)) return fail(COSMICA_ERR_INVALID, "item %u: T must be > 0", i);
-        its[i] = DevItem{w.T_GeVn, w.first_pid, w.seed, w.param_idx, w.species_idx};
+        const cosmica_params &p = b->params[w.param_idx];
+        const bool own = w.r0_AU != 0.0;
+        if (own && !valid_start(p, w.r0_AU, w.th0_rad, w.ph0_rad))
+            return fail(COSMICA_ERR_INVALID, "item %u: start position outside the heliosphere", i);
+        its[i] = make_item(w.T_GeVn, w.first_pid, w.seed, w.param_idx, w.species_idx, own ? w.r0_AU : p.r0_AU,
+                           own ? w.th0_rad : p.th0_rad, own ? w.ph0_rad : p.ph0_rad, i);
         pre[i + 1] = pre[i] + w.n;
     }
     return COSMICA_OK;

@@ -101,6 +101,25 @@ cosmica_status check_params(const cosmica_params *p);
 cosmica_status check_species(const cosmica_species *s);
 DevParams to_dev(const cosmica_params &p);
 DevSpecies to_dev(const cosmica_species &s);
+// a start position inside the heliosphere of p: r_in <= r0 < R_out, th0 in (0, pi), finite ph0
+bool valid_start(const cosmica_params &p, double r0, double th0, double ph0);
+
+inline DevItem make_item(double T, uint64_t first_pid, uint64_t seed, uint32_t param_idx, uint32_t species_idx,
+                         double r0, double th0, double ph0, uint32_t out_item)
+{
+    DevItem it;
+    it.T = T;
+    it.first_pid = first_pid;
+    it.seed = seed;
+    it.param_idx = param_idx;
+    it.species_idx = species_idx;
+    it.r0 = r0;
+    it.th0 = th0;
+    it.ph0 = ph0;
+    it.out_item = out_item;
+    it.pad = 0;
+    return it;
+}
 int num_sms();
 
 }  // namespace host

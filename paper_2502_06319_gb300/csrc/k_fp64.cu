@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(128) k_propagate_fp64(const DevParams *__restr
         const DevSpecies sp = spc[item.species_idx];
         const uint64_t pid = item.first_pid + (g - prefix[it]);
         m64::State x;
-        m64::init_state(p, sp, item.T, x);
+        m64::init_state(sp, item.T, item.r0, item.th0, item.ph0, x);
         while (x.status == COSMICA_PATH_RUNNING) m64::em_step(p, sp, item.seed, pid, x);
         out.r[g] = x.r;
         out.th[g] = x.th;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(128) k_propagate_fp64(const DevParams *__restr
         out.s[g] = x.s;
         out.steps[g] = x.k;
         out.status[g] = (uint8_t)x.status;
-        out.item[g] = it;
+        out.item[g] = item.out_item;
         if (out.lw) out.lw[g] = -x.Lam;
         my_steps = x.k;
     }

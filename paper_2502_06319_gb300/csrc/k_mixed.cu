@@ -38,12 +38,12 @@ __device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t q, 
     L.pid = item.first_pid + local;
     L.seed = item.seed;
     L.g = a.prefix[it] + local;
-    L.item = it;
+    L.item = item.out_item;
     L.k = 0;
     L.max_steps = (uint32_t)p.max_steps;
     const double T = item.T;
     const double P0 = sp.A / fabs(sp.Z) * sqrt(T * (T + 2.0 * sp.m0));
-    x.init(p.r0, p.th0, p.ph0, log(P0), p.R_out, p.f.r_in);
+    x.init(item.r0, item.th0, item.ph0, log(P0), p.R_out, p.f.r_in);
     en.init(T, (float)sp.m0, sp.aoz);
 }
 

@@ -96,7 +96,7 @@ extern "C" cosmica_status cosmica_propagate_noalloc(const cosmica_params *params
     prefix[0] = 0;
     for (uint32_t e = 0; e < n_energies; ++e) {
         if (!(std::isfinite(T_in[e]) && T_in[e] > 0.0)) return fail(COSMICA_ERR_INVALID, "T_in[%u] must be > 0", e);
-        items[e] = DevItem{T_in[e], prefix[e], seed, 0u, 0u};
+        items[e] = make_item(T_in[e], prefix[e], seed, 0u, 0u, params->r0_AU, params->th0_rad, params->ph0_rad, e);
         prefix[e + 1] = prefix[e] + n_per_energy[e];
     }
     const uint64_t total = prefix[n_energies];

@@ -332,9 +332,10 @@ __device__ __forceinline__ void em_step(const DevParams &p, const DevSpecies &sp
     }
 }
 
-__device__ __forceinline__ void init_state(const DevParams &p, const DevSpecies &sp, double T, State &x)
+__device__ __forceinline__ void init_state(const DevSpecies &sp, double T, double r0, double th0, double ph0,
+                                           State &x)
 {
-    x.r = p.r0; x.th = p.th0; x.ph = p.ph0;
+    x.r = r0; x.th = th0; x.ph = ph0;
     const double P0 = sp.A / fabs(sp.Z) * sqrt(T * (T + 2.0 * sp.m0));
     x.lnP = dm::log(P0);
     x.T = T;
