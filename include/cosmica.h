@@ -36,6 +36,7 @@ extern "C" {
 #endif
 
 #define COSMICA_ABI_VERSION 1u
+#define COSMICA_MAX_SHELLS 16u
 
 typedef enum {
     COSMICA_OK = 0,
@@ -126,6 +127,21 @@ typedef struct {
                                   L = (2V/(3r))(1 + beta^2) accumulated for the
                                   weight of Eq. 4; needs exit->lw)              */
     int32_t reserved0;
+    /* Radial shells of the inner heliosphere (Sec. II.B: shells that the wind
+     * fills during successive Carrington rotations, each with its own
+     * parameters).  n_shells = 0: one region with K0 and tilt_deg above.
+     * n_shells = n >= 1: n equal shells between the Sun and the termination
+     * shock (the outer boundary when there is none), shell k = 0 innermost;
+     * the outermost continues beyond the shock.  K0 and the sheet tilt of
+     * shell k are shell_K0[k] and shell_tilt_deg[k] (K0 and tilt_deg above are
+     * then unused); across each interior edge R_e they pass from shell e-1's
+     * to shell e's value along the cubic smoothstep over [R_e - w, R_e + w],
+     * w = shell_blend_AU (needs 0 < 2w < shell width). */
+    uint32_t n_shells;         /* 0 .. COSMICA_MAX_SHELLS                   */
+    uint32_t reserved1;
+    double shell_blend_AU;
+    double shell_K0[COSMICA_MAX_SHELLS];        /* AU^2/day, > 0            */
+    double shell_tilt_deg[COSMICA_MAX_SHELLS];  /* |tilt| < 89              */
 } cosmica_params;
 
 /* Particle species: mass number A, signed charge number Z, rest mass per

@@ -59,6 +59,8 @@
 #define ORC_STEP_LIMIT 2
 #define ORC_NONFINITE  3
 
+#define ORC_MAX_SHELLS 16
+
 /* Model parameters.  Every field is a double so that the Python side can
  * build it from a flat list; flags are 0.0 / 1.0. */
 typedef struct {
@@ -94,6 +96,11 @@ typedef struct {
     double ph0;           /* rad, start longitude                                */
     double formulation;   /* 0: momentum form (Eq. 5-6, L = 0); 1: energy form
                              (Eq. 1: T-SDE with the loss weight of Eq. 4)         */
+    double n_shells;      /* radial shells of the inner heliosphere (Sec. II.B);
+                             0: one region with K0 and tilt_deg above             */
+    double shell_blend_AU;/* half-width of the blend at each interior shell edge */
+    double shell_K0[ORC_MAX_SHELLS];       /* K0 of shell k, innermost first      */
+    double shell_tilt_deg[ORC_MAX_SHELLS]; /* sheet tilt of shell k               */
 } orc_params;
 
 typedef struct {
@@ -396,6 +403,39 @@ static double field_B0(const orc_params *p)
     return p->B1AU_nT / sqrt(1.0 + G0 * G0);
 }
 
+/* Radial shells of the inner heliosphere (Sec. II.B: the region inside the
+ * termination shock is split into expanding shells, one per Carrington
+ * rotation of the wind that fills it, each with its own parameters).
+ * Reading: n equal shells between the Sun and the termination shock (the
+ * outer boundary when there is none); shell k holds v[k]; the outermost
+ * shell continues beyond the shock.  Across each interior edge R_e = e dR the
+ * value passes from v[e-1] to v[e] along the cubic smoothstep
+ * S(x) = x^2 (3 - 2x), x = (r - R_e + w) / (2w), over [R_e - w, R_e + w]:
+ * continuous with its first derivative, which is all the drift terms use. */
+static void shell_value(const orc_params *p, const double *v, double r, double *val, double *dval)
+{
+    int n = (int)p->n_shells;
+    double R_edge = (p->R_ts > 0.0) ? p->R_ts : p->R_out;
+    double dR = R_edge / n;
+    double w = p->shell_blend_AU;
+    int k = (int)floor(r / dR);
+    if (k > n - 1) k = n - 1;
+    if (k < 0) k = 0;
+    int lo = -1;   /* inner shell of the edge whose blend window holds r */
+    if (k >= 1 && r < k * dR + w) lo = k - 1;
+    else if (k + 1 <= n - 1 && r > (k + 1) * dR - w) lo = k;
+    if (lo < 0) {
+        *val = v[k];
+        *dval = 0.0;
+        return;
+    }
+    double x = (r - ((lo + 1) * dR - w)) / (2.0 * w);
+    double S = x * x * (3.0 - 2.0 * x);
+    double dS = 6.0 * x * (1.0 - x) / (2.0 * w);
+    *val = v[lo] + (v[lo + 1] - v[lo]) * S;
+    *dval = (v[lo + 1] - v[lo]) * dS;
+}
+
 /* Evaluate every coefficient of Eq. 3 at (r, th, ph, lnP). */
 static void eval_coef(const orc_params *p, const orc_species *sp,
                       double r, double th, double ph, double lnP, orc_coef *c)
@@ -424,10 +464,18 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
         c->dg_dr = 0.0;
     }
 
-    /* parallel diffusion K_par = K0 beta P g(r) */
-    double Kbase = p->K0 * c->beta * c->P;
+    /* the shell holding r sets K0 and the sheet tilt */
+    double K0 = p->K0, dK0_dr = 0.0, tilt = p->tilt_deg, dtilt_dr = 0.0;
+    if (p->n_shells > 0.0) {
+        shell_value(p, p->shell_K0, r, &K0, &dK0_dr);
+        shell_value(p, p->shell_tilt_deg, r, &tilt, &dtilt_dr);
+    }
+
+    /* parallel diffusion K_par = K0(r) beta P g(r) */
+    double Kbase = K0 * c->beta * c->P;
     c->Kpar = Kbase * c->g;
     double dKpar_dr = Kbase * c->dg_dr;
+    if (p->n_shells > 0.0) dKpar_dr = dKpar_dr + dK0_dr * c->beta * c->P * c->g;
     double dKpar_dth = 0.0;
 
     if (p->isotropic != 0.0) {
@@ -519,8 +567,9 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
     if (p->isotropic == 0.0 && p->hcs_on != 0.0) {
         double Omega = ORC_TWO_PI / p->rot_period_day;
         double sa, ca;
-        orc_sincos(p->tilt_deg * ORC_DEG, &sa, &ca);
+        orc_sincos(tilt * ORC_DEG, &sa, &ca);
         double ta = sa / ca;
+        double dta_dr = (1.0 + ta * ta) * dtilt_dr * ORC_DEG;   /* shells: tilt varies with r */
         double phs = ph + Omega * r / c->V;
         double dphs_dr = Omega / c->V;
         double dphs_dth = -Omega * r * c->dV_dth / (c->V * c->V);
@@ -528,6 +577,7 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
         orc_sincos(phs, &sp_, &cp_);
         double th_cs = 0.5 * ORC_PI + orc_atan(ta * sp_);
         double dthcs = ta * cp_ / (1.0 + ta * ta * sp_ * sp_);   /* d th_cs / d phs */
+        double dthcs_dta = sp_ / (1.0 + ta * ta * sp_ * sp_);    /* d th_cs / d tan(alpha) */
         /* half-width: max(2 r_L / r, delta_min), r_L = P/(c |B|) */
         double D = c->P * 1e9 / (ORC_C_MS * B0 * 1e-9 * ORC_AU_M);
         double G = c->Gam, one_G2 = 1.0 + G * G;
@@ -545,6 +595,7 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
         double u = (th_cs - th) / delta;
         double h = orc_tanh(u);
         double du_dr = (dthcs * dphs_dr - u * dd_dr) / delta;
+        if (p->n_shells > 0.0) du_dr = du_dr + dthcs_dta * dta_dr / delta;
         double du_dth = (dthcs * dphs_dth - 1.0 - u * dd_dth) / delta;
         double du_dph = dthcs / delta;
         c->h = h;

@@ -35,7 +35,10 @@ PARAM_FIELDS = (
     "ts_K_factor", "r_in", "dt_max", "dt_fixed", "max_steps", "isotropic",
     "V_const_kms", "eps_adv", "eps_diff", "dt_min", "dlat_deg", "dts_AU",
     "dcs_min_deg", "rot_period_day", "r0", "th0", "ph0", "formulation",
+    "n_shells", "shell_blend_AU",
 )
+MAX_SHELLS = 16
+SHELL_ARRAYS = ("shell_K0", "shell_tilt_deg")
 
 EXIT, STEP_LIMIT, NONFINITE = 1, 2, 3
 
@@ -53,7 +56,7 @@ EVAL_NAMES = (
 
 
 class OrcParams(C.Structure):
-    _fields_ = [(n, C.c_double) for n in PARAM_FIELDS]
+    _fields_ = [(n, C.c_double) for n in PARAM_FIELDS] + [(n, C.c_double * MAX_SHELLS) for n in SHELL_ARRAYS]
 
 
 class OrcSpecies(C.Structure):
@@ -105,7 +108,11 @@ def lib():
 
 
 def _params(p: dict) -> OrcParams:
-    return OrcParams(*[float(p[n]) for n in PARAM_FIELDS])
+    o = OrcParams(*[float(p[n]) for n in PARAM_FIELDS])
+    for n in SHELL_ARRAYS:
+        vals = [float(x) for x in p.get(n, ())]
+        getattr(o, n)[:] = (vals + [0.0] * MAX_SHELLS)[:MAX_SHELLS]
+    return o
 
 
 def _species(s: dict) -> OrcSpecies:

@@ -50,10 +50,22 @@ def f_lis(species, P):
 
 
 def solve(species, K0, V_kms, r_in, R, r0, P0_list, n_r=1200, dlnP=2e-3, P_top=1e4):
-    """Modulated J(T0) at r0 for each rigidity in P0_list (GV)."""
+    """Modulated J(T0) at r0 for each rigidity in P0_list (GV).
+
+    K0 is a number, or a function of r (array in, array out) for a radially
+    varying diffusion normalisation K = K0(r) beta P.  In the latter case the
+    radial operator is discretised in conservative (flux) form,
+    (1/r^2)[(r^2 K)_{i+1/2}(f_{i+1} - f_i) - (r^2 K)_{i-1/2}(f_i - f_{i-1})]/h^2,
+    which needs K at the cell faces only and no derivative of K."""
     V = V_kms * DAY_S / AU_KM
     r = np.linspace(r_in, R, n_r + 1)
     h = r[1] - r[0]
+    flux = callable(K0)
+    if flux:
+        K0_face = np.asarray(K0(np.concatenate([[r[0] - 0.5 * h], r + 0.5 * h])), np.float64)
+        r_face = np.concatenate([[r[0] - 0.5 * h], r + 0.5 * h])
+        w_lo = r_face[:-1] ** 2 * K0_face[:-1] / (r ** 2 * h ** 2)   # (r^2 K0)_{i-1/2} / (r_i^2 h^2)
+        w_up = r_face[1:] ** 2 * K0_face[1:] / (r ** 2 * h ** 2)     # (r^2 K0)_{i+1/2} / (r_i^2 h^2)
     P0_list = np.asarray(P0_list, np.float64)
     y_top = math.log(P_top)
     y_bot = math.log(P0_list.min()) - 2 * dlnP
@@ -63,8 +75,16 @@ def solve(species, K0, V_kms, r_in, R, r0, P0_list, n_r=1200, dlnP=2e-3, P_top=1
     def coeffs(y):
         P = math.exp(y)
         b, _ = _beta_T(species, P)
-        K = K0 * b * P
         a = 3.0 * r / (2.0 * V)                # prefactor
+        if flux:
+            bP = b * P
+            lo = a * (bP * w_lo + V / (2 * h))
+            up = a * (bP * w_up - V / (2 * h))
+            di = -a * bP * (w_lo + w_up)
+            # reflecting inner boundary: ghost f_{-1} = f_1
+            up0 = lo[0] + up[0]
+            return lo, di, up, up0
+        K = K0 * b * P
         c2 = a * K                             # of f_rr
         c1 = a * (2.0 * K / r - V)             # of f_r
         lo = c2 / h ** 2 - c1 / (2 * h)        # coefficient of f_{i-1}

@@ -40,6 +40,8 @@ class cosmica_params(C.Structure):
         ("rot_period_day", C.c_double), ("r0_AU", C.c_double), ("th0_rad", C.c_double), ("ph0_rad", C.c_double),
         ("max_steps", C.c_uint32), ("precision", C.c_int32), ("formulation", C.c_int32),
         ("reserved0", C.c_int32),
+        ("n_shells", C.c_uint32), ("reserved1", C.c_uint32), ("shell_blend_AU", C.c_double),
+        ("shell_K0", C.c_double * 16), ("shell_tilt_deg", C.c_double * 16),
     ]
 
 
@@ -200,9 +202,11 @@ _PARAM_MAP = {
     "eps_adv": "eps_adv", "eps_diff": "eps_diff", "V_const_kms": "V_const_kms", "dlat_deg": "dlat_deg",
     "dts_AU": "dts_AU", "dcs_min_deg": "dcs_min_deg", "rot_period_day": "rot_period_day",
     "r0": "r0_AU", "th0": "th0_rad", "ph0": "ph0_rad", "max_steps": "max_steps",
-    "formulation": "formulation",
+    "formulation": "formulation", "n_shells": "n_shells", "shell_blend_AU": "shell_blend_AU",
+    "shell_K0": "shell_K0", "shell_tilt_deg": "shell_tilt_deg",
 }
-_INT_FIELDS = {"polarity", "drift_on", "hcs_on", "isotropic", "max_steps", "formulation"}
+_INT_FIELDS = {"polarity", "drift_on", "hcs_on", "isotropic", "max_steps", "formulation", "n_shells"}
+_ARRAY_FIELDS = {"shell_K0", "shell_tilt_deg"}
 
 
 def make_params(d: dict, precision: int = PREC_FP64) -> cosmica_params:
@@ -210,7 +214,11 @@ def make_params(d: dict, precision: int = PREC_FP64) -> cosmica_params:
     lib().cosmica_params_default(C.byref(p))
     for k, v in d.items():
         f = _PARAM_MAP[k]
-        setattr(p, f, int(round(v)) if f in _INT_FIELDS else float(v))
+        if f in _ARRAY_FIELDS:
+            vals = [float(x) for x in v]
+            getattr(p, f)[:] = (vals + [0.0] * 16)[:16]
+        else:
+            setattr(p, f, int(round(v)) if f in _INT_FIELDS else float(v))
     p.precision = int(precision)
     return p
 

@@ -43,6 +43,11 @@ struct alignas(16) F32Params {
     float drift, hcs;          // 0 / 1
     float sqrt2er;             // sqrt(2 er)
     float pad0, pad1;
+    // radial shells (n_sh = 0: none); edge e at e * sh_dr, blend half-width sh_w
+    float n_sh, sh_dr, sh_inv_dr, sh_w, sh_inv_2w;
+    float pad2, pad3, pad4;
+    float sh_K0[COSMICA_MAX_SHELLS];      // AU^2/day
+    float sh_alpha[COSMICA_MAX_SHELLS];   // sheet tilt [rad]
 };
 
 struct DevParams {
@@ -52,6 +57,8 @@ struct DevParams {
     double R_out, R_ts, ts_f, r_in, dt_max, dt_fixed, dt_min, eps_adv, eps_diff;
     double V_const_kms, dlat_deg, dts, dcs_min_deg, rot_period, r0, th0, ph0, max_steps;
     double formulation;        // 0 momentum form, 1 energy form
+    double n_shells, shell_w;  // radial shells (0: one region), blend half-width [AU]
+    double shell_K0[COSMICA_MAX_SHELLS], shell_tilt_deg[COSMICA_MAX_SHELLS];
     int32_t precision, pad;
     // derived on the device
     double B0;                 // nT, |B|(1 AU, equator) = B1AU

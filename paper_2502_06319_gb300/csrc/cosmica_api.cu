@@ -86,6 +86,19 @@ cosmica_status check_params(const cosmica_params *p)
         return fail(COSMICA_ERR_INVALID, "unknown precision %d", p->precision);
     if (p->formulation != 0 && p->formulation != 1)
         return fail(COSMICA_ERR_INVALID, "formulation %d: 0 (momentum) or 1 (energy)", p->formulation);
+    if (p->n_shells > COSMICA_MAX_SHELLS)
+        return fail(COSMICA_ERR_INVALID, "n_shells %u exceeds %u", p->n_shells, COSMICA_MAX_SHELLS);
+    if (p->n_shells > 0) {
+        const double edge = p->R_ts_AU > 0.0 ? p->R_ts_AU : p->R_out_AU;
+        const double width = edge / (double)p->n_shells;
+        if (p->n_shells > 1 && !(pos(p->shell_blend_AU) && 2.0 * p->shell_blend_AU < width))
+            return fail(COSMICA_ERR_INVALID, "need 0 < 2 shell_blend_AU < shell width %g AU", width);
+        for (uint32_t k = 0; k < p->n_shells; ++k) {
+            if (!pos(p->shell_K0[k])) return fail(COSMICA_ERR_INVALID, "shell_K0[%u] must be > 0", k);
+            if (!(std::fabs(p->shell_tilt_deg[k]) < 89.0))
+                return fail(COSMICA_ERR_INVALID, "shell_tilt_deg[%u]: need |tilt| < 89 deg", k);
+        }
+    }
     if (!p->isotropic) {
         if (!(pos(p->V_slow_kms) && pos(p->V_fast_kms) && pos(p->B1AU_nT) && pos(p->rot_period_day) &&
               pos(p->dlat_deg)))
@@ -130,6 +143,12 @@ DevParams to_dev(const cosmica_params &p)
     d.dlat_deg = p.dlat_deg; d.dts = p.dts_AU; d.dcs_min_deg = p.dcs_min_deg; d.rot_period = p.rot_period_day;
     d.r0 = p.r0_AU; d.th0 = p.th0_rad; d.ph0 = p.ph0_rad; d.max_steps = (double)p.max_steps;
     d.formulation = (double)p.formulation;
+    d.n_shells = (double)p.n_shells;
+    d.shell_w = p.shell_blend_AU;
+    for (uint32_t k = 0; k < COSMICA_MAX_SHELLS; ++k) {
+        d.shell_K0[k] = p.shell_K0[k];
+        d.shell_tilt_deg[k] = p.shell_tilt_deg[k];
+    }
     d.precision = p.precision;
     return d;
 }
@@ -254,6 +273,16 @@ struct Tables {
     }
 };
 
+// K0 of the region holding radius r (the shell's, when the model has shells).
+static double start_K0(const cosmica_params &p, double r)
+{
+    if (p.n_shells == 0) return p.K0;
+    const double edge = p.R_ts_AU > 0.0 ? p.R_ts_AU : p.R_out_AU;
+    const double k = std::floor(r / (edge / (double)p.n_shells));
+    const uint32_t i = (uint32_t)std::min(std::max(k, 0.0), (double)(p.n_shells - 1));
+    return p.shell_K0[i];
+}
+
 // Queue order with the longest expected paths first: items sorted by K0 beta0 P0
 // ascending (a smaller diffusion coefficient at the start means more steps).
 std::vector<uint32_t> cost_order(const std::vector<DevItem> &its, const cosmica_params *prm,
@@ -267,7 +296,7 @@ std::vector<uint32_t> cost_order(const std::vector<DevItem> &its, const cosmica_
         const double pn = std::sqrt(T * (T + 2.0 * sp.m0_GeV));
         const double P = aoz * pn;
         const double beta = pn / (T + sp.m0_GeV);
-        key[i] = {prm[its[i].param_idx].K0 * beta * P, (uint32_t)i};
+        key[i] = {start_K0(prm[its[i].param_idx], its[i].r0) * beta * P, (uint32_t)i};
     }
     std::stable_sort(key.begin(), key.end(),
                      [](const std::pair<double, uint32_t> &a, const std::pair<double, uint32_t> &b) {
@@ -290,12 +319,12 @@ int num_sms()
     return g_num_sms;
 }
 
-PersistentShape shape_for(int acc, const cosmica_tuning *t, uint64_t n_total)
+PersistentShape shape_for(MixedVariant v, const cosmica_tuning *t, uint64_t n_total)
 {
     unsigned block = (t && t->block) ? t->block : 128u;
     const unsigned period = t ? t->compact_period : 64u;
     block = std::min(256u, std::max(32u, block / 32u * 32u));
-    int max_b = mixed_max_blocks_per_sm(acc, block, period != 0);
+    int max_b = mixed_max_blocks_per_sm(v, block, period != 0);
     if (max_b < 1) max_b = 1;
     int bps = (t && t->blocks_per_sm) ? (int)t->blocks_per_sm : max_b;
     bps = std::min(bps, max_b);
@@ -364,6 +393,8 @@ extern "C" void cosmica_params_default(cosmica_params *p)
     p->ph0_rad = 0.0;
     p->max_steps = 100000000u;
     p->precision = COSMICA_PREC_FP64;
+    p->n_shells = 0;
+    p->shell_blend_AU = 0.5;
 }
 
 static cosmica_status upload_params(const cosmica_params *ps, uint32_t n, DevParams **out)
@@ -464,8 +495,8 @@ static cosmica_status propagate_items(cosmica_model *m, const cosmica_species *s
     if (m->p.precision == COSMICA_PREC_FP64) {
         e = launch_propagate_fp64(a, s);
     } else {
-        e = launch_propagate_mixed(a, m->p.precision, m->p.formulation == 1,
-                                   shape_for(m->p.precision, nullptr, total), s);
+        const MixedVariant v{m->p.precision, m->p.formulation == 1, m->p.n_shells > 0};
+        e = launch_propagate_mixed(a, v, shape_for(v, nullptr, total), s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
     if (host_out) return ExitStage::copy_back(ex, out, s);
@@ -694,9 +725,11 @@ struct cosmica_batch {
     std::vector<cosmica_params> params;
     std::vector<cosmica_species> species;
     int precision = 0;
+    bool shells = false;       // some parameter set has radial shells
     DevParams *d_prm = nullptr;
     DevSpecies *d_spc = nullptr;
     Tables tab;
+    MixedVariant variant() const { return MixedVariant{precision, params[0].formulation == 1, shells}; }
     ExitStage exit_stage;
     DevBuf spec_items, lis_buf;
     Staging spec_stage, lis_stage;
@@ -730,6 +763,7 @@ extern "C" cosmica_status cosmica_batch_create(const cosmica_params *params, uin
     b->params.assign(params, params + n_params);
     b->species.assign(species, species + n_species);
     b->precision = params[0].precision;
+    for (uint32_t i = 0; i < n_params; ++i) b->shells = b->shells || params[i].n_shells > 0;
     cosmica_status st = upload_params(params, n_params, &b->d_prm);
     if (st == COSMICA_OK) {
         std::vector<DevSpecies> hs(n_species);
@@ -793,14 +827,13 @@ static cosmica_status batch_launch(cosmica_batch *b, uint64_t total, const ExitP
         CK(cudaMemsetAsync(b->tab.counters, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
         cudaError_t e = (b->precision == COSMICA_PREC_FP64)
                             ? launch_propagate_fp64(a, s)
-                            : launch_propagate_mixed(a, b->precision, b->params[0].formulation == 1,
-                                                     shape_for(b->precision, tuning, total), s);
+                            : launch_propagate_mixed(a, b->variant(), shape_for(b->variant(), tuning, total), s);
         if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
         return COSMICA_OK;
     };
     const bool graph = tuning && tuning->use_graph && s != nullptr;
     if (!graph) return direct();
-    const PersistentShape sh = shape_for(b->precision, tuning, total);
+    const PersistentShape sh = shape_for(b->variant(), tuning, total);
     auto key = std::make_tuple(total, b->tab.n_items, (const void *)ex.lw, (const void *)b->tab.dev.d, sh.block,
                                sh.grid * 1024u + sh.compact_period, s, b->precision);
     if (!b->gexec || b->gkey != key) {
@@ -889,11 +922,12 @@ extern "C" cosmica_status cosmica_batch_spectrum(cosmica_batch *b, const cosmica
 
 // =============================================================== autotune ==
 // Tuned shapes are cached per (device, configuration class): the precision,
-// whether the sets have a drift / a termination shock, and the particle count
-// to within a factor of two (it sets the particles per lane, hence the tail).
+// whether the sets have a drift / a termination shock, the particle count to
+// within a factor of two (it sets the particles per lane, hence the tail), and
+// the kernel variant (energy form, radial shells).
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, std::pair<cosmica_tuning, double>> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int, int>, std::pair<cosmica_tuning, double>> g_tune_cache;
 }  // namespace
 
 extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_item *items, uint32_t n_items,
@@ -911,7 +945,9 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
     for (uint32_t i = 0; i < n_items && items; ++i) n_all += items[i].n;
     int size_class = 0;
     while ((n_all >> size_class) > 1) ++size_class;
-    const auto key = std::make_tuple(dev, b->precision, drift, ts, size_class);
+    // the kernel variant (energy form, shells) has its own registers, hence its own best shape
+    const int variant = (b->params[0].formulation == 1 ? 1 : 0) | (b->shells ? 2 : 0);
+    const auto key = std::make_tuple(dev, b->precision, drift, ts, size_class, variant);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -964,7 +1000,7 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
         std::vector<cosmica_tuning> cands;
         for (unsigned blk : blocks) {
             for (unsigned per : periods) {
-                const unsigned maxb = (unsigned)std::max(1, mixed_max_blocks_per_sm(b->precision, blk, per != 0));
+                const unsigned maxb = (unsigned)std::max(1, mixed_max_blocks_per_sm(b->variant(), blk, per != 0));
                 cands.push_back(cosmica_tuning{blk, maxb, per, 0, 1});
                 if (maxb / 2 >= 1 && maxb / 2 != maxb) cands.push_back(cosmica_tuning{blk, maxb / 2, per, 0, 1});
             }

@@ -79,8 +79,14 @@ cudaError_t launch_derive(DevParams *prm, uint32_t n, cudaStream_t s);
 cudaError_t launch_propagate_fp64(const LaunchArgs &a, cudaStream_t s);
 
 // mixed precision persistent kernel; acc = COSMICA_PREC_MIXED or COSMICA_PREC_MIXED_F64ACC
-cudaError_t launch_propagate_mixed(const LaunchArgs &a, int acc, bool energy, PersistentShape shape, cudaStream_t s);
-int mixed_max_blocks_per_sm(int acc, unsigned block, bool compact);
+// compile-time variant of the mixed kernel a launch needs
+struct MixedVariant {
+    int acc;        // COSMICA_PREC_MIXED or COSMICA_PREC_MIXED_F64ACC
+    bool energy;    // energy formulation (Eq. 1) instead of the momentum form
+    bool shells;    // some parameter set of the launch has radial shells
+};
+cudaError_t launch_propagate_mixed(const LaunchArgs &a, MixedVariant v, PersistentShape shape, cudaStream_t s);
+int mixed_max_blocks_per_sm(MixedVariant v, unsigned block, bool compact);
 
 cudaError_t launch_histogram(const ExitPtrs &ex, uint64_t n, uint32_t n_items, uint32_t nbins, double x_lo,
                              double dx, unsigned long long *hist, cudaStream_t s);

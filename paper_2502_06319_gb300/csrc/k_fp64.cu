@@ -56,6 +56,18 @@ __global__ void k_derive(DevParams *prm, uint32_t n)
     f.hcs = hcs ? 1.0f : 0.0f;
     f.sqrt2er = (float)sqrt(2.0 * (double)f.er);
     f.pad0 = f.pad1 = 0.0f;
+    const int ns = (int)p.n_shells;
+    const double dR = ns > 0 ? ((p.R_ts > 0.0) ? p.R_ts : p.R_out) / ns : 1.0;
+    f.n_sh = (float)ns;
+    f.sh_dr = (float)dR;
+    f.sh_inv_dr = (float)(1.0 / dR);
+    f.sh_w = (float)p.shell_w;
+    f.sh_inv_2w = ns > 1 ? (float)(1.0 / (2.0 * p.shell_w)) : 0.0f;
+    f.pad2 = f.pad3 = f.pad4 = 0.0f;
+    for (int k = 0; k < COSMICA_MAX_SHELLS; ++k) {
+        f.sh_K0[k] = (float)p.shell_K0[k];
+        f.sh_alpha[k] = (float)(p.shell_tilt_deg[k] * kDeg);
+    }
 }
 
 __global__ void __launch_bounds__(128) k_propagate_fp64(const DevParams *__restrict__ prm,

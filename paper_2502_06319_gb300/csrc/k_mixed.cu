@@ -11,6 +11,7 @@
 // quasi-particle mapping (Sec. IV.A) is kept; its one-launch-per-energy-bin
 // loop (Sec. IV.A, last paragraph) becomes this single launch.
 #include <cstdint>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -49,7 +50,7 @@ __device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t q, 
 
 // One Euler-Maruyama step (Eq. 3, Eq. 6) of an active lane; true when the path ended
 // (exit record written).
-template <int ACC, bool EN>
+template <int ACC, bool EN, bool SH>
 __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, EnergyAcc<ACC, EN> &en,
                                      unsigned long long &my_steps)
 {
@@ -65,7 +66,7 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
     } else {
         lnP = x.flnP();
     }
-    m32::eval(q, L.M2, L.sq, x.fr(), x.fth(), x.fph(), lnP, c);
+    m32::eval<SH>(q, L.M2, L.sq, x.fr(), x.fth(), x.fph(), lnP, c);
     const float sdt = sqrtf(c.dt);
     const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
     const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);
@@ -110,7 +111,7 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
 // they need, repacked through shared memory into the block's lowest lanes, so that
 // issued warp instructions keep carrying full lanes while the long tail of exit
 // times plays out.  Both phases share one step site (one copy of the step code).
-template <int ACC, bool COMPACT, bool EN>
+template <int ACC, bool COMPACT, bool EN, bool SH>
 __global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a, uint32_t period)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a, uint32_t 
             // an idle warp goes straight to the next checkpoint
             tick = __any_sync(0xffffffffu, active) ? (tick + 1 == period ? 0 : tick + 1) : 0;
         }
-        if (active && step<ACC, EN>(a, L, x, en, my_steps)) active = false;
+        if (active && step<ACC, EN, SH>(a, L, x, en, my_steps)) active = false;
     }
     if (a.steps_total) {
         for (int o = 16; o > 0; o >>= 1) my_steps += __shfl_down_sync(0xffffffffu, my_steps, o);
@@ -215,7 +216,7 @@ __global__ void k_debug_eval32(const DevParams *__restrict__ prm, const DevSpeci
     if (i >= n) return;
     float dbg[kDebugEvalN];
     m32::Drift c;
-    m32::eval(prm[0].f, spc[0].aoz_m0_sq, spc[0].sgnq, (float)st[4 * i], (float)st[4 * i + 1],
+    m32::eval<true>(prm[0].f, spc[0].aoz_m0_sq, spc[0].sgnq, (float)st[4 * i], (float)st[4 * i + 1],
               (float)st[4 * i + 2], (float)st[4 * i + 3], c, dbg);
     for (int j = 0; j < kDebugEvalN; ++j) out[(size_t)i * kDebugEvalN + j] = dbg[j];
 }
@@ -225,44 +226,49 @@ __global__ void k_debug_eval32(const DevParams *__restrict__ prm, const DevSpeci
 template <int ACC, bool EN>
 static size_t pack_bytes(unsigned block) { return (size_t)block * sizeof(Packed<ACC, EN>); }
 
-template <int ACC, bool COMPACT>
-static int occupancy(unsigned block)
+// Call fn(acc, compact, energy, shells) with each flag as a compile-time constant.
+template <class Fn>
+static void visit_variant(MixedVariant v, bool compact, Fn &&fn)
+{
+    auto on_acc = [&](auto A) {
+        auto on_compact = [&](auto C) {
+            auto on_energy = [&](auto E) {
+                if (v.shells) fn(A, C, E, std::true_type{});
+                else fn(A, C, E, std::false_type{});
+            };
+            if (v.energy) on_energy(std::true_type{});
+            else on_energy(std::false_type{});
+        };
+        if (compact) on_compact(std::true_type{});
+        else on_compact(std::false_type{});
+    };
+    if (v.acc == COSMICA_PREC_MIXED_F64ACC) on_acc(std::integral_constant<int, COSMICA_PREC_MIXED_F64ACC>{});
+    else on_acc(std::integral_constant<int, COSMICA_PREC_MIXED>{});
+}
+
+int mixed_max_blocks_per_sm(MixedVariant v, unsigned block, bool compact)
 {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<ACC, COMPACT, false>, (int)block,
-                                                  COMPACT ? pack_bytes<ACC, false>(block) : 0);
+    visit_variant(v, compact, [&](auto A, auto C, auto E, auto S) {
+        constexpr int acc = decltype(A)::value;
+        constexpr bool c = decltype(C)::value, en = decltype(E)::value, sh = decltype(S)::value;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<acc, c, en, sh>, (int)block,
+                                                      c ? pack_bytes<acc, en>(block) : 0);
+    });
     return nb;
 }
 
-int mixed_max_blocks_per_sm(int acc, unsigned block, bool compact)
-{
-    if (acc == COSMICA_PREC_MIXED_F64ACC)
-        return compact ? occupancy<COSMICA_PREC_MIXED_F64ACC, true>(block)
-                       : occupancy<COSMICA_PREC_MIXED_F64ACC, false>(block);
-    return compact ? occupancy<COSMICA_PREC_MIXED, true>(block) : occupancy<COSMICA_PREC_MIXED, false>(block);
-}
-
-template <int ACC, bool EN>
-static void launch_variant(const LaunchArgs &a, PersistentShape shape, cudaStream_t s)
-{
-    const uint32_t per = shape.compact_period;
-    if (per)
-        k_propagate_mixed<ACC, true, EN><<<shape.grid, shape.block, pack_bytes<ACC, EN>(shape.block), s>>>(a, per);
-    else
-        k_propagate_mixed<ACC, false, EN><<<shape.grid, shape.block, 0, s>>>(a, 1);
-}
-
-cudaError_t launch_propagate_mixed(const LaunchArgs &a, int acc, bool energy, PersistentShape shape, cudaStream_t s)
+cudaError_t launch_propagate_mixed(const LaunchArgs &a, MixedVariant v, PersistentShape shape, cudaStream_t s)
 {
     if (a.n_total == 0) return cudaSuccess;
     cudaGetLastError();
-    if (acc == COSMICA_PREC_MIXED_F64ACC) {
-        if (energy) launch_variant<COSMICA_PREC_MIXED_F64ACC, true>(a, shape, s);
-        else launch_variant<COSMICA_PREC_MIXED_F64ACC, false>(a, shape, s);
-    } else {
-        if (energy) launch_variant<COSMICA_PREC_MIXED, true>(a, shape, s);
-        else launch_variant<COSMICA_PREC_MIXED, false>(a, shape, s);
-    }
+    const uint32_t per = shape.compact_period;
+    visit_variant(v, per != 0, [&](auto A, auto C, auto E, auto S) {
+        constexpr int acc = decltype(A)::value;
+        constexpr bool c = decltype(C)::value, en = decltype(E)::value, sh = decltype(S)::value;
+        k_propagate_mixed<acc, c, en, sh><<<shape.grid, shape.block, c ? pack_bytes<acc, en>(shape.block) : 0, s>>>(
+            a, c ? per : 1u);
+    });
     note_launch();
     return cudaGetLastError();
 }

@@ -138,11 +138,11 @@ extern "C" cosmica_status cosmica_propagate_noalloc(const cosmica_params *params
         e = launch_propagate_fp64(a, s);
     } else {
         const unsigned block = 128;
-        const int bps = std::max(1, mixed_max_blocks_per_sm(params->precision, block, true));
+        const MixedVariant v{params->precision, params->formulation == 1, params->n_shells > 0};
+        const int bps = std::max(1, mixed_max_blocks_per_sm(v, block, true));
         uint64_t grid = (uint64_t)num_sms() * (uint64_t)bps;
         grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (total + block - 1) / block));
-        e = launch_propagate_mixed(a, params->precision, params->formulation == 1,
-                                   PersistentShape{block, (unsigned)grid, 64u}, s);
+        e = launch_propagate_mixed(a, v, PersistentShape{block, (unsigned)grid, 64u}, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "cosmica_propagate_noalloc launch");
     return COSMICA_OK;

@@ -49,8 +49,34 @@ struct Drift {
     float beta;        // speed / c at the start of the step
 };
 
+// Radial shells (Sec. II.B): the shells a, b whose values blend at r and the
+// smoothstep weight S(x) = x^2 (3 - 2x) with its radial derivative; a = b and
+// S = 0 away from the edge windows, so v[a] + (v[b] - v[a]) S is the shell's value.
+__device__ __forceinline__ void shell_weights(const F32Params &q, float r, int &a, int &b, float &S, float &dS)
+{
+    const int n = (int)q.n_sh;
+    const int k = min(max((int)(r * q.sh_inv_dr), 0), n - 1);
+    float x = 0.0f;
+    a = k;
+    b = k;
+    const float lo_edge = (float)k * q.sh_dr;
+    const float hi_edge = (float)(k + 1) * q.sh_dr;
+    if (k >= 1 && r < lo_edge + q.sh_w) {
+        a = k - 1;
+        x = (r - (lo_edge - q.sh_w)) * q.sh_inv_2w;
+    } else if (k + 1 <= n - 1 && r > hi_edge - q.sh_w) {
+        b = k + 1;
+        x = (r - (hi_edge - q.sh_w)) * q.sh_inv_2w;
+    }
+    S = x * x * fmaf(-2.0f, x, 3.0f);
+    dS = 6.0f * x * (1.0f - x) * q.sh_inv_2w;
+}
+
 // Coefficients at (r, th, ph, lnP).  q: FP32 constants of the heliosphere.
 // M2 = (A/|Z| m0)^2, sq = sign of the charge.
+// SH: the parameter sets of the launch may have radial shells (compile-time, so
+// that single-region launches carry none of the shell code or its registers).
+template <bool SH>
 __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, float r, float th, float ph,
                                      float lnP, Drift &o, float *dbg = nullptr)
 {
@@ -85,10 +111,30 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
         dg = -q.ts_drop * 2.0f * st * (1.0f - st) * q.inv_dts;
     }
 
+    // radial shells: K0 and the sheet tilt of the shell holding r (the single-region
+    // tilt is read where the sheet needs it, so that it is not live before)
+    const bool shells = SH && q.n_sh != 0.0f;
+    float K0 = q.K0, dK0 = 0.0f, sh_ta = 0.0f, sh_ta2 = 0.0f, dta = 0.0f;
+    if (shells) {
+        int a, b;
+        float S, dS;
+        shell_weights(q, r, a, b, S, dS);
+        const float Ka = q.sh_K0[a], dKab = q.sh_K0[b] - Ka;
+        K0 = fmaf(dKab, S, Ka);
+        dK0 = dKab * dS;
+        const float al = q.sh_alpha[a], dal = q.sh_alpha[b] - al;
+        float sa, ca;
+        __sincosf(fmaf(dal, S, al), &sa, &ca);
+        sh_ta = __fdividef(sa, ca);
+        sh_ta2 = sh_ta * sh_ta;
+        dta = fmaf(sh_ta, sh_ta, 1.0f) * dal * dS;
+    }
+
     // diffusion tensor in (r, th, ph); K_rth = K_thph = 0
-    const float Kb = q.K0 * beta * P;
+    const float Kb = K0 * beta * P;
     const float Kpar = Kb * g;
-    const float dKpar = Kb * dg;
+    float dKpar = Kb * dg;
+    if (shells) dKpar = fmaf(dK0 * beta * P, g, dKpar);
     const float c2s = fmaf(q.er, G2 * iq, iq);            // cos^2 + er sin^2
     const float iq2 = iq * iq;
     const float dc2_dr = -2.0f * G2 * iq2 * inv_r;         // d cos^2 psi / dr
@@ -133,8 +179,11 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
             const float red = fmaf(-kTwoPiF, turns, phs);
             float sp, cp;
             __sincosf(red, &sp, &cp);
-            const float th_cs = kHalfPiF + atanf(q.ta * sp);
-            const float dthcs = __fdividef(q.ta * cp, fmaf(q.ta2, sp * sp, 1.0f));
+            const float ta = shells ? sh_ta : q.ta;
+            const float ta2 = shells ? sh_ta2 : q.ta2;
+            const float th_cs = kHalfPiF + atanf(ta * sp);
+            const float inv_den = __fdividef(1.0f, fmaf(ta2, sp * sp, 1.0f));
+            const float dthcs = (ta * cp) * inv_den;
             const float sqiq = sqrtf(iq);
             const float w_rl = q.D2 * P * r * sqiq;
             float dd_dr = 0.0f, dd_dth = 0.0f;
@@ -151,7 +200,9 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
             const float sh = half_one_plus_tanh(u);
             h = fmaf(2.0f, sh, -1.0f);
             const float sech2 = 4.0f * sh * (1.0f - sh);
-            hr = sech2 * fmaf(dthcs, dphs_dr, -u * dd_dr) * inv_d;
+            float ur = fmaf(dthcs, dphs_dr, -u * dd_dr);
+            if (shells) ur = fmaf(sp * inv_den, dta, ur);    // the tilt changes with r
+            hr = sech2 * ur * inv_d;
             ht = sech2 * fmaf(-u, dd_dth, fmaf(dthcs, dphs_dth, -1.0f)) * inv_d;
             hp = sech2 * dthcs * inv_d;
         }

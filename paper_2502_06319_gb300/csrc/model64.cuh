@@ -68,6 +68,36 @@ __device__ __forceinline__ double field_B0(const DevParams &p)
     return p.B1AU / sqrt(1.0 + G0 * G0);
 }
 
+// Radial shells of the inner heliosphere (Sec. II.B): n equal shells out to the
+// termination shock (the outer boundary without one), shell k holding v[k], the
+// outermost continuing beyond; across interior edge R_e = e dR the value passes
+// from v[e-1] to v[e] along S(x) = x^2 (3 - 2x), x = (r - R_e + w)/(2w), over
+// [R_e - w, R_e + w].  Same operations, in the same order, as the definition.
+__device__ __forceinline__ void shell_value(const DevParams &p, const double *v, double r, double *val,
+                                            double *dval)
+{
+    const int n = (int)p.n_shells;
+    const double R_edge = (p.R_ts > 0.0) ? p.R_ts : p.R_out;
+    const double dR = R_edge / n;
+    const double w = p.shell_w;
+    int k = (int)floor(r / dR);
+    if (k > n - 1) k = n - 1;
+    if (k < 0) k = 0;
+    int lo = -1;
+    if (k >= 1 && r < k * dR + w) lo = k - 1;
+    else if (k + 1 <= n - 1 && r > (k + 1) * dR - w) lo = k;
+    if (lo < 0) {
+        *val = v[k];
+        *dval = 0.0;
+        return;
+    }
+    const double x = (r - ((lo + 1) * dR - w)) / (2.0 * w);
+    const double S = x * x * (3.0 - 2.0 * x);
+    const double dS = 6.0 * x * (1.0 - x) / (2.0 * w);
+    *val = v[lo] + (v[lo + 1] - v[lo]) * S;
+    *dval = (v[lo + 1] - v[lo]) * dS;
+}
+
 __device__ __forceinline__ void eval(const DevParams &p, const DevSpecies &sp, double r, double th,
                                      double ph, double lnP, Coef &c)
 {
@@ -94,9 +124,16 @@ __device__ __forceinline__ void eval(const DevParams &p, const DevSpecies &sp, d
         dg_dr = 0.0;
     }
 
-    const double Kbase = p.K0 * beta * P;
+    // the shell holding r sets K0 and the sheet tilt
+    double K0 = p.K0, dK0_dr = 0.0, tilt = p.tilt_deg, dtilt_dr = 0.0;
+    if (p.n_shells > 0.0) {
+        shell_value(p, p.shell_K0, r, &K0, &dK0_dr);
+        shell_value(p, p.shell_tilt_deg, r, &tilt, &dtilt_dr);
+    }
+    const double Kbase = K0 * beta * P;
     const double Kpar = Kbase * g;
-    const double dKpar_dr = Kbase * dg_dr;
+    double dKpar_dr = Kbase * dg_dr;
+    if (p.n_shells > 0.0) dKpar_dr = dKpar_dr + dK0_dr * beta * P * g;
     const double dKpar_dth = 0.0;
     c.Kpar = Kpar;
 
@@ -166,8 +203,9 @@ __device__ __forceinline__ void eval(const DevParams &p, const DevSpecies &sp, d
     if (p.isotropic == 0.0 && p.hcs_on != 0.0) {
         const double Omega = kTwoPi / p.rot_period;
         double sa, ca;
-        dm::sincos(p.tilt_deg * kDeg, &sa, &ca);
+        dm::sincos(tilt * kDeg, &sa, &ca);
         const double ta = sa / ca;
+        const double dta_dr = (1.0 + ta * ta) * dtilt_dr * kDeg;
         const double phs = ph + Omega * r / c.V;
         const double dphs_dr = Omega / c.V;
         const double dphs_dth = -Omega * r * c.dV_dth / (c.V * c.V);
@@ -175,6 +213,7 @@ __device__ __forceinline__ void eval(const DevParams &p, const DevSpecies &sp, d
         dm::sincos(phs, &sp_, &cp_);
         const double th_cs = 0.5 * kPi + dm::atan(ta * sp_);
         const double dthcs = ta * cp_ / (1.0 + ta * ta * sp_ * sp_);
+        const double dthcs_dta = sp_ / (1.0 + ta * ta * sp_ * sp_);
         const double D = P * 1e9 / (kC_ms * B0 * 1e-9 * kAU_m);
         const double G = c.Gam, one_G2 = 1.0 + G * G;
         const double w_rl = 2.0 * D * r / sqrt(one_G2);
@@ -189,7 +228,8 @@ __device__ __forceinline__ void eval(const DevParams &p, const DevSpecies &sp, d
         }
         const double u = (th_cs - th) / delta;
         h = dm::tanh(u);
-        const double du_dr = (dthcs * dphs_dr - u * dd_dr) / delta;
+        double du_dr = (dthcs * dphs_dr - u * dd_dr) / delta;
+        if (p.n_shells > 0.0) du_dr = du_dr + dthcs_dta * dta_dr / delta;
         const double du_dth = (dthcs * dphs_dth - 1.0 - u * dd_dth) / delta;
         const double du_dph = dthcs / delta;
         dh_dr = (1.0 - h * h) * du_dr;

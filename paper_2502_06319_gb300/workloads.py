@@ -33,7 +33,10 @@ PARAM_FIELDS = (
     "ts_K_factor", "r_in", "dt_max", "dt_fixed", "max_steps", "isotropic",
     "V_const_kms", "eps_adv", "eps_diff", "dt_min", "dlat_deg", "dts_AU",
     "dcs_min_deg", "rot_period_day", "r0", "th0", "ph0", "formulation",
+    "n_shells", "shell_blend_AU",
 )
+MAX_SHELLS = 16
+SHELL_ARRAYS = ("shell_K0", "shell_tilt_deg")   # per-shell tables (lists of up to 16 values)
 
 DEFAULT_PARAMS: Dict[str, float] = {
     "K0": 11.5,             # AU^2/day
@@ -67,6 +70,10 @@ DEFAULT_PARAMS: Dict[str, float] = {
     "th0": math.pi / 2.0,
     "ph0": 0.0,
     "formulation": 0.0,     # 0: momentum form (Eq. 5-6); 1: energy form with loss weight (Eq. 1, Eq. 4)
+    "n_shells": 0.0,        # radial shells of the inner heliosphere (0: one region)
+    "shell_blend_AU": 0.5,  # half-width of the blend across each interior shell edge
+    "shell_K0": (),         # K0 of each shell [AU^2/day], innermost first
+    "shell_tilt_deg": (),   # current-sheet tilt of each shell [deg]
 }
 
 
@@ -75,7 +82,7 @@ def params(**overrides) -> Dict[str, float]:
     for k, v in overrides.items():
         if k not in p:
             raise KeyError(f"unknown parameter {k!r}")
-        p[k] = float(v)
+        p[k] = tuple(float(x) for x in v) if k in SHELL_ARRAYS else float(v)
     return p
 
 
@@ -159,6 +166,56 @@ def config3(seed: int = 20250210, n_sets: int = 64, n_e: int = 30,
             jobs.append(Job(p, SPECIES[sname], T, counts,
                             seed=seed * 1000 + len(jobs), bins=Bins(0.1, 1000.0, 512),
                             name=f"c3/{i}/{sname}", mixed=True))
+    return jobs
+
+
+# ------------------------------------------------ time-dependent shells --
+CARRINGTON_DAYS = 27.26     # synodic rotation period (Sec. II.B)
+CYCLE_ROTATIONS = 147.3     # ~11-year solar cycle in Carrington rotations
+
+
+def solar_cycle_series(seed: int = 20250212, n_rot: int = 200) -> Dict[str, List[float]]:
+    """Synthetic solar activity per Carrington rotation (the paper's HelMod tables are
+    not available): activity a = sin^2(pi c / 147.3); current-sheet tilt 8 + 62 a deg and
+    diffusion normalisation K0 = 30 - 22 a AU^2/day, each with seeded noise and clipped to
+    config 3's ranges ([5, 75] deg, [5, 30] AU^2/day)."""
+    rng = np.random.default_rng(seed)
+    c = np.arange(n_rot)
+    a = np.sin(np.pi * c / CYCLE_ROTATIONS) ** 2
+    tilt = np.clip(8.0 + 62.0 * a + rng.normal(0.0, 3.0, n_rot), 5.0, 75.0)
+    K0 = np.clip(30.0 - 22.0 * a + rng.normal(0.0, 1.0, n_rot), 5.0, 30.0)
+    return {"K0": [float(x) for x in K0], "tilt_deg": [float(x) for x in tilt]}
+
+
+def shell_params(series, rotation: int, n_shells: int = 15, **overrides) -> Dict[str, float]:
+    """Heliosphere observed at Carrington rotation `rotation`: shell k (innermost k = 0)
+    holds the conditions of rotation `rotation - k`, whose wind fills it (Sec. II.B)."""
+    if rotation - (n_shells - 1) < 0:
+        raise ValueError("the series must reach n_shells - 1 rotations back")
+    K0 = [series["K0"][rotation - k] for k in range(n_shells)]
+    tilt = [series["tilt_deg"][rotation - k] for k in range(n_shells)]
+    base = dict(R_ts=85.0, ts_K_factor=0.5, R_out=122.0, K0=K0[0], tilt_deg=tilt[0],
+                n_shells=n_shells, shell_K0=K0, shell_tilt_deg=tilt)
+    base.update(overrides)
+    return params(**base)
+
+
+def config_shells(seed: int = 20250212, first_rotation: int = 40, n_obs: int = 13, n_e: int = 30,
+                  n_lo: int = 1_000, n_hi: int = 50_000, scale: float = 1.0) -> List[Job]:
+    """Time-dependent batch: one observation per Carrington rotation over a year (13
+    rotations), each a heliosphere of 15 radial shells from the synthetic solar-cycle
+    series; protons and He-4, 30 energies, log-uniform counts in [n_lo, n_hi]."""
+    ser = solar_cycle_series(seed)
+    rng = np.random.default_rng(seed + 1)
+    T = logspace(0.1, 100.0, n_e)
+    jobs = []
+    for i in range(n_obs):
+        p = shell_params(ser, first_rotation + i)
+        for sname in ("proton", "he4"):
+            counts = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), n_e))
+            counts = [max(1, int(round(c * scale))) for c in counts]
+            jobs.append(Job(p, SPECIES[sname], T, counts, seed=seed * 1000 + len(jobs),
+                            bins=Bins(0.1, 1000.0, 512), name=f"shells/{i}/{sname}", mixed=True))
     return jobs
 
 

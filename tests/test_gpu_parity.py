@@ -106,6 +106,7 @@ MODELS = {
     "ts_tilt60": W.params(R_ts=85.0, R_out=122.0, tilt_deg=60.0, polarity=-1.0),
     "unipolar": W.params(hcs_on=0.0),
     "nodrift": W.params(drift_on=0.0),
+    "shells": W.shell_params(W.solar_cycle_series(), rotation=60),
 }
 
 

@@ -95,12 +95,15 @@ def test_tensor_is_rotated_diagonal_and_cholesky(orc, model):
 
 @pytest.mark.parametrize("model", ["full", "ts", "aniso_th"])
 def test_ito_drift_from_cartesian_divergence(orc, model):
-    p = _models()[model]
-    sp = W.PROTON
-    lnP = math.log(2.0)
-    for (r, th, ph) in POINTS:
+    check_ito_drift(orc, _models()[model], W.PROTON, math.log(2.0), POINTS)
+
+
+def check_ito_drift(orc, p, sp, lnP, points, hrel=3e-5):
+    """Coordinate Ito drift and noise covariance against Cartesian finite differences
+    (step hrel * r; truncation error falls as its square)."""
+    for (r, th, ph) in points:
         x = _cart(r, th, ph)
-        hstep = 3e-5 * r
+        hstep = hrel * r
         # div K (Cartesian): d_i K_ij
         divK = np.zeros(3)
         for i in range(3):
@@ -157,11 +160,16 @@ def _div(f, x, hstep):
 @pytest.mark.parametrize("model", ["full", "ts", "unipolar", "aniso_th"])
 @pytest.mark.parametrize("sp", SPECIES, ids=["p", "he4", "e"])
 def test_drift_is_curl_and_divergence_free(orc, model, sp):
-    p = _models()[model]
+    check_drift_curl(orc, _models()[model], sp, POINTS, model)
+
+
+def check_drift_curl(orc, p, sp, points, model="", hrel=2e-6):
+    """Drift = sgn(qA) curl(kappa_A h e_B) by finite differences (step hrel * r), and
+    divergence-free."""
     for lnP in (math.log(0.5), math.log(20.0)):
-        for (r, th, ph) in POINTS:
+        for (r, th, ph) in points:
             x = _cart(r, th, ph)
-            hstep = 2e-6 * r
+            hstep = hrel * r
             e = orc.evaluate(p, sp, r, th, ph, lnP)
             Q = _basis(th, ph)
             vd = Q @ np.array([e["vdr"], e["vdth"], e["vdph"]])
@@ -176,7 +184,7 @@ def test_drift_is_curl_and_divergence_free(orc, model, sp):
                 return _basis(tt, pp) @ np.array([ee["vdr"], ee["vdth"], ee["vdph"]])
 
             # the sheet is thin: a small step keeps the O(h^2) truncation negligible
-            div = _div(vd_cart, x, 1e-6 * r)
+            div = _div(vd_cart, x, min(1e-6, hrel) * r)
             assert abs(div) < 1e-4 * np.linalg.norm(vd) / r + 1e-12, (div, np.linalg.norm(vd))
 
 
