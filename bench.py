@@ -58,9 +58,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "shells"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "shells", "squashed"],
                     help="shells: 13 monthly observations of a 15-shell time-dependent heliosphere "
-                         "(Sec. II.B), proton + He-4, batched like config 3")
+                         "(Sec. II.B), proton + He-4, batched like config 3; squashed: config 3 with "
+                         "the nose-squashed shock and outer boundary (Sec. II.B)")
     ap.add_argument("--c4-requests", type=int, default=24, help="requests per serving run")
     ap.add_argument("--c3-scale", type=float, default=1.0, help="scale of config-3 particle counts")
     ap.add_argument("--scale", type=float, default=1.0, help="scale of config-1/2 particles per energy")
@@ -86,6 +87,11 @@ def workload(args):
     if args.workload == "c2":
         n = max(1, int(round(20000 * args.scale)))
         return [W.config2(n)], f"config2: full model, proton, 30 energies x {n}"
+    if args.workload == "squashed":
+        jobs = W.config3(scale=args.c3_scale, geometry=W.SQUASHED)
+        return jobs, (f"squashed: config3 (64 heliospheres x 3 species x 30 energies) with the nose-squashed "
+                      f"shock (85 AU nose, x1.35 tail, x1.15 flank) and boundary (122 AU, x1.6, x1.25), "
+                      f"scale {args.c3_scale}")
     if args.workload == "shells":
         jobs = W.config_shells(scale=args.c3_scale)
         return jobs, (f"shells: 13 Carrington rotations x 15 radial shells (synthetic solar cycle, seed 20250212) "

@@ -142,6 +142,20 @@ typedef struct {
     double shell_blend_AU;
     double shell_K0[COSMICA_MAX_SHELLS];        /* AU^2/day, > 0            */
     double shell_tilt_deg[COSMICA_MAX_SHELLS];  /* |tilt| < 89              */
+    /* Nose-squashed heliosphere (Sec. II.B: inner heliosphere and heliosheath
+     * squashed toward the nose, the Sun's direction of motion through the
+     * interstellar medium).  squashed = 1: the termination shock and the outer
+     * boundary are spheroids about the nose axis with the Sun on the axis:
+     * nose distance R (R_ts_AU, R_out_AU), tail distance R * tail_ratio, flank
+     * semi-axis R * flank_ratio (semi-axis R (1 + tail)/2 along the axis,
+     * centre R (tail - 1)/2 behind the Sun).  The shock factor uses the shock's
+     * distance along the direction of the point; a path exits when it is
+     * outside the outer spheroid.  The start point must lie inside it. */
+    int32_t squashed;          /* 0: spheres (R_ts_AU, R_out_AU); 1: spheroids */
+    int32_t reserved2;
+    double nose_th_rad, nose_ph_rad;            /* nose direction            */
+    double ts_tail_ratio, ts_flank_ratio;       /* > 0                        */
+    double hp_tail_ratio, hp_flank_ratio;       /* > 0                        */
 } cosmica_params;
 
 /* Particle species: mass number A, signed charge number Z, rest mass per

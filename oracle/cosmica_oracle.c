@@ -99,6 +99,14 @@ typedef struct {
     double n_shells;      /* radial shells of the inner heliosphere (Sec. II.B);
                              0: one region with K0 and tilt_deg above             */
     double shell_blend_AU;/* half-width of the blend at each interior shell edge */
+    double squashed;      /* 1: termination shock and outer boundary are spheroids
+                             squashed toward the nose (Sec. II.B); 0: spheres     */
+    double nose_th;       /* rad, colatitude of the nose direction              */
+    double nose_ph;       /* rad, longitude of the nose direction               */
+    double ts_tail;       /* tail distance / nose distance (R_ts) of the shock   */
+    double ts_flank;      /* flank semi-axis / nose distance of the shock        */
+    double hp_tail;       /* the same for the outer boundary (R_out at the nose) */
+    double hp_flank;
     double shell_K0[ORC_MAX_SHELLS];       /* K0 of shell k, innermost first      */
     double shell_tilt_deg[ORC_MAX_SHELLS]; /* sheet tilt of shell k               */
 } orc_params;
@@ -360,9 +368,10 @@ typedef struct {
     double Bmag, Br, Bph;         /* field [nT]: |B|, signed components   */
     double h, dh_dr, dh_dth, dh_dph, delta_cs; /* sheet polarity and width */
     double g, dg_dr;              /* termination-shock diffusion factor   */
+    double dg_dth, dg_dph;        /* its angular derivatives (squashed shock) */
     double Kpar;                  /* AU^2/day                              */
     double K[3][3];               /* physical components, order r,th,ph   */
-    double dKdr[3][3], dKdth[3][3];
+    double dKdr[3][3], dKdth[3][3], dKdph[3][3];
     double Adiv[3];               /* (1/sqrt g) d_j (sqrt g K^ij), coordinate form */
     double L[3][3];               /* lower Cholesky factor of 2K          */
     double W[3];                  /* kappa_A h e_B, physical components   */
@@ -436,6 +445,43 @@ static void shell_value(const orc_params *p, const double *v, double r, double *
     *dval = (v[lo + 1] - v[lo]) * dS;
 }
 
+/* Nose-squashed heliosphere (Sec. II.B: the inner heliosphere and the
+ * heliosheath are both squashed in the nose direction, the Sun's direction of
+ * motion through the interstellar medium).  Reading: each surface is a spheroid
+ * about the nose axis n, with the Sun on its axis, nose distance R, tail
+ * distance R t and flank semi-axis R f: semi-axis a = R (1 + t)/2 along n,
+ * b = R f across, centre at distance c = R (t - 1)/2 behind the Sun.  With
+ * mu = cos(angle between the position and n), a point at radius r is outside
+ * when (r mu + c)^2 / a^2 + r^2 (1 - mu^2) / b^2 >= 1. */
+static double nose_mu(const orc_params *p, double th, double ph, double *dmu_dth, double *dmu_dph)
+{
+    double st, ct, sn, cn, sd, cd;
+    orc_sincos(th, &st, &ct);
+    orc_sincos(p->nose_th, &sn, &cn);
+    orc_sincos(ph - p->nose_ph, &sd, &cd);
+    if (dmu_dth) *dmu_dth = ct * sn * cd - st * cn;
+    if (dmu_dph) *dmu_dph = -st * sn * sd;
+    return st * sn * cd + ct * cn;
+}
+
+/* Distance R(mu) from the Sun to the spheroid (nose distance R, ratios t, f)
+ * along the direction mu, and dR/dmu: the positive root of
+ * A R^2 + 2 B R + C = 0, A = mu^2/a^2 + (1 - mu^2)/b^2, B = mu c / a^2,
+ * C = c^2/a^2 - 1 < 0, written as R = -C / (B + sqrt(B^2 - A C)). */
+static double spheroid_radius(double R, double t, double f, double mu, double *dR_dmu)
+{
+    double a = R * (1.0 + t) / 2.0, b = R * f, c = R * (t - 1.0) / 2.0;
+    double A = mu * mu / (a * a) + (1.0 - mu * mu) / (b * b);
+    double B = mu * c / (a * a);
+    double C = c * c / (a * a) - 1.0;
+    double Rm = -C / (B + sqrt(B * B - A * C));
+    if (dR_dmu) {
+        double dF_dmu = Rm * Rm * mu * (1.0 / (a * a) - 1.0 / (b * b)) + Rm * c / (a * a);
+        *dR_dmu = -dF_dmu / (A * Rm + B);
+    }
+    return Rm;
+}
+
 /* Evaluate every coefficient of Eq. 3 at (r, th, ph, lnP). */
 static void eval_coef(const orc_params *p, const orc_species *sp,
                       double r, double th, double ph, double lnP, orc_coef *c)
@@ -454,8 +500,21 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
     /* wind */
     wind(p, th, &c->V, &c->dV_dth);
 
-    /* termination shock: g(r) = 1 - (1 - f)(1 + tanh((r - Rts)/d))/2 */
-    if (p->R_ts > 0.0) {
+    /* termination shock: g = 1 - (1 - f)(1 + tanh((r - Rts)/d))/2, with Rts the shock's
+     * distance along the direction of the point when the heliosphere is squashed */
+    c->dg_dth = 0.0;
+    c->dg_dph = 0.0;
+    if (p->R_ts > 0.0 && p->squashed != 0.0) {
+        double dmu_dth, dmu_dph, dR_dmu;
+        double mu = nose_mu(p, th, ph, &dmu_dth, &dmu_dph);
+        double Rts = spheroid_radius(p->R_ts, p->ts_tail, p->ts_flank, mu, &dR_dmu);
+        double t = orc_tanh((r - Rts) / p->dts_AU);
+        double sech2 = 1.0 - t * t;
+        c->g = 1.0 - (1.0 - p->ts_K_factor) * 0.5 * (1.0 + t);
+        c->dg_dr = -(1.0 - p->ts_K_factor) * 0.5 * sech2 / p->dts_AU;
+        c->dg_dth = (1.0 - p->ts_K_factor) * 0.5 * sech2 / p->dts_AU * dR_dmu * dmu_dth;
+        c->dg_dph = (1.0 - p->ts_K_factor) * 0.5 * sech2 / p->dts_AU * dR_dmu * dmu_dph;
+    } else if (p->R_ts > 0.0) {
         double t = orc_tanh((r - p->R_ts) / p->dts_AU);
         c->g = 1.0 - (1.0 - p->ts_K_factor) * 0.5 * (1.0 + t);
         c->dg_dr = -(1.0 - p->ts_K_factor) * 0.5 * (1.0 - t * t) / p->dts_AU;
@@ -476,7 +535,8 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
     c->Kpar = Kbase * c->g;
     double dKpar_dr = Kbase * c->dg_dr;
     if (p->n_shells > 0.0) dKpar_dr = dKpar_dr + dK0_dr * c->beta * c->P * c->g;
-    double dKpar_dth = 0.0;
+    double dKpar_dth = Kbase * c->dg_dth;
+    double dKpar_dph = Kbase * c->dg_dph;
 
     if (p->isotropic != 0.0) {
         /* K = K_par * identity */
@@ -484,6 +544,7 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
             c->K[i][i] = c->Kpar;
             c->dKdr[i][i] = dKpar_dr;
             c->dKdth[i][i] = dKpar_dth;
+            c->dKdph[i][i] = dKpar_dph;
         }
         c->Gam = 0.0;
     } else {
@@ -523,15 +584,22 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
         c->dKdth[2][2] = dKpar_dth * s2 + c->Kpar * ds2_dth + dKpr_dth * c2 + Kpr * dc2_dth;
         c->dKdth[0][2] = (dKpr_dth - dKpar_dth) * sc + (Kpr - c->Kpar) * dsc_dth;
         c->dKdth[1][1] = dKpt_dth;
+        /* only g depends on ph (squashed shock); the spiral does not */
+        double dKpr_dph = er * dKpar_dph, dKpt_dph = et * dKpar_dph;
+        c->dKdph[0][0] = dKpar_dph * c2 + dKpr_dph * s2;
+        c->dKdph[2][2] = dKpar_dph * s2 + dKpr_dph * c2;
+        c->dKdph[0][2] = (dKpr_dph - dKpar_dph) * sc;
+        c->dKdph[1][1] = dKpt_dph;
     }
     /* symmetric completion */
     c->K[1][0] = c->K[0][1];  c->K[2][0] = c->K[0][2];  c->K[2][1] = c->K[1][2];
     c->dKdr[1][0] = c->dKdr[0][1]; c->dKdr[2][0] = c->dKdr[0][2]; c->dKdr[2][1] = c->dKdr[1][2];
     c->dKdth[1][0] = c->dKdth[0][1]; c->dKdth[2][0] = c->dKdth[0][2]; c->dKdth[2][1] = c->dKdth[1][2];
+    c->dKdph[1][0] = c->dKdph[0][1]; c->dKdph[2][0] = c->dKdph[0][2]; c->dKdph[2][1] = c->dKdph[1][2];
 
     /* Ito drift of the diffusion term in (r, th, ph): A^i = (1/sqrt g) d_j (sqrt g K^ij),
-     * sqrt g = r^2 sin(th), K^ij = K_(ij) / (h_i h_j), h = (1, r, r sin th),
-     * d_ph K = 0 (axisymmetric model). */
+     * sqrt g = r^2 sin(th), K^ij = K_(ij) / (h_i h_j), h = (1, r, r sin th).
+     * d_ph K = 0 except through a squashed shock, whose terms d_ph K^(i ph) are added. */
     {
         const double (*K)[3] = (const double (*)[3])c->K;
         const double (*Kr)[3] = (const double (*)[3])c->dKdr;
@@ -539,6 +607,12 @@ static void eval_coef(const orc_params *p, const orc_species *sp,
         c->Adiv[0] = Kr[0][0] + 2.0 * K[0][0] / r + Kt[0][1] / r + K[0][1] * cot_th / r;
         c->Adiv[1] = (Kt[1][1] + K[1][1] * cot_th) / (r * r) + Kr[0][1] / r + K[0][1] / (r * r);
         c->Adiv[2] = (Kr[0][2] + K[0][2] / r) / (r * sin_th) + Kt[1][2] / (r * r * sin_th);
+        if (p->squashed != 0.0) {
+            const double (*Kp)[3] = (const double (*)[3])c->dKdph;
+            c->Adiv[0] = c->Adiv[0] + Kp[0][2] / (r * sin_th);
+            c->Adiv[1] = c->Adiv[1] + Kp[1][2] / (r * r * sin_th);
+            c->Adiv[2] = c->Adiv[2] + Kp[2][2] / (r * r * sin_th * sin_th);
+        }
     }
 
     /* C = B B^T = 2K: lower Cholesky factor (Eq. 3) */
@@ -674,6 +748,7 @@ enum {
     OE_L00, OE_L10, OE_L11, OE_L20, OE_L21, OE_L22,
     OE_WR, OE_WPH, OE_VDR, OE_VDTH, OE_VDPH,
     OE_DLNP, OE_ARTOT, OE_DT,
+    OE_DG_DTH, OE_DG_DPH,
     OE_N
 };
 
@@ -699,6 +774,7 @@ void orc_eval(const orc_params *p, const orc_species *sp,
     out[OE_WR] = c.W[0]; out[OE_WPH] = c.W[2];
     out[OE_VDR] = c.vd[0]; out[OE_VDTH] = c.vd[1]; out[OE_VDPH] = c.vd[2];
     out[OE_DLNP] = c.dlnP; out[OE_ARTOT] = c.Ar_tot; out[OE_DT] = c.dt;
+    out[OE_DG_DTH] = c.dg_dth; out[OE_DG_DPH] = c.dg_dph;
 }
 
 /* ======================================================================= */
@@ -713,6 +789,17 @@ typedef struct {
     uint32_t k;
     int status;
 } orc_state;
+
+/* Outer boundary: r >= R_out, or outside the squashed outer spheroid. */
+static int outside(const orc_params *p, double r, double th, double ph)
+{
+    if (p->squashed == 0.0) return r >= p->R_out;
+    double mu = nose_mu(p, th, ph, 0, 0);
+    double a = p->R_out * (1.0 + p->hp_tail) / 2.0, b = p->R_out * p->hp_flank;
+    double c = p->R_out * (p->hp_tail - 1.0) / 2.0;
+    double xa = r * mu + c;
+    return xa * xa / (a * a) + r * r * (1.0 - mu * mu) / (b * b) >= 1.0;
+}
 
 static void em_step(const orc_params *p, const orc_species *sp, uint64_t seed, uint64_t pid,
                     orc_state *x, double *dt_out)
@@ -766,7 +853,7 @@ static void em_step(const orc_params *p, const orc_species *sp, uint64_t seed, u
     x->k = x->k + 1u;
     if (!(isfinite(x->r) && isfinite(x->th) && isfinite(x->ph) && isfinite(x->lnP) && isfinite(x->s))) {
         x->status = ORC_NONFINITE;
-    } else if (x->r >= p->R_out) {
+    } else if (outside(p, x->r, x->th, x->ph)) {
         x->status = ORC_EXIT;
     } else if ((double)x->k >= p->max_steps) {
         x->status = ORC_STEP_LIMIT;

@@ -36,6 +36,7 @@ PARAM_FIELDS = (
     "V_const_kms", "eps_adv", "eps_diff", "dt_min", "dlat_deg", "dts_AU",
     "dcs_min_deg", "rot_period_day", "r0", "th0", "ph0", "formulation",
     "n_shells", "shell_blend_AU",
+    "squashed", "nose_th", "nose_ph", "ts_tail", "ts_flank", "hp_tail", "hp_flank",
 )
 MAX_SHELLS = 16
 SHELL_ARRAYS = ("shell_K0", "shell_tilt_deg")
@@ -52,6 +53,7 @@ EVAL_NAMES = (
     "L00", "L10", "L11", "L20", "L21", "L22",
     "Wr", "Wph", "vdr", "vdth", "vdph",
     "dlnP", "Ar_tot", "dt",
+    "dg_dth", "dg_dph",
 )
 
 

@@ -42,6 +42,9 @@ class cosmica_params(C.Structure):
         ("reserved0", C.c_int32),
         ("n_shells", C.c_uint32), ("reserved1", C.c_uint32), ("shell_blend_AU", C.c_double),
         ("shell_K0", C.c_double * 16), ("shell_tilt_deg", C.c_double * 16),
+        ("squashed", C.c_int32), ("reserved2", C.c_int32), ("nose_th_rad", C.c_double), ("nose_ph_rad", C.c_double),
+        ("ts_tail_ratio", C.c_double), ("ts_flank_ratio", C.c_double), ("hp_tail_ratio", C.c_double),
+        ("hp_flank_ratio", C.c_double),
     ]
 
 
@@ -204,8 +207,10 @@ _PARAM_MAP = {
     "r0": "r0_AU", "th0": "th0_rad", "ph0": "ph0_rad", "max_steps": "max_steps",
     "formulation": "formulation", "n_shells": "n_shells", "shell_blend_AU": "shell_blend_AU",
     "shell_K0": "shell_K0", "shell_tilt_deg": "shell_tilt_deg",
+    "squashed": "squashed", "nose_th": "nose_th_rad", "nose_ph": "nose_ph_rad", "ts_tail": "ts_tail_ratio",
+    "ts_flank": "ts_flank_ratio", "hp_tail": "hp_tail_ratio", "hp_flank": "hp_flank_ratio",
 }
-_INT_FIELDS = {"polarity", "drift_on", "hcs_on", "isotropic", "max_steps", "formulation", "n_shells"}
+_INT_FIELDS = {"polarity", "drift_on", "hcs_on", "isotropic", "max_steps", "formulation", "n_shells", "squashed"}
 _ARRAY_FIELDS = {"shell_K0", "shell_tilt_deg"}
 
 

@@ -48,6 +48,11 @@ struct alignas(16) F32Params {
     float pad2, pad3, pad4;
     float sh_K0[COSMICA_MAX_SHELLS];      // AU^2/day
     float sh_alpha[COSMICA_MAX_SHELLS];   // sheet tilt [rad]
+    // nose-squashed spheroids (sq = 0: spheres): nose direction, and per surface the
+    // centre offset c behind the Sun and 1/a^2, 1/b^2 of its semi-axes
+    // (the shock's spheroid in units of its nose distance ts_R, C = c^2/a^2 - 1)
+    float sq, nose_ph, sin_nth, cos_nth;
+    float ts_R, ts_c, ts_ia2, ts_ib2, ts_C, hp_c, hp_ia2, hp_ib2;
 };
 
 struct DevParams {
@@ -58,6 +63,7 @@ struct DevParams {
     double V_const_kms, dlat_deg, dts, dcs_min_deg, rot_period, r0, th0, ph0, max_steps;
     double formulation;        // 0 momentum form, 1 energy form
     double n_shells, shell_w;  // radial shells (0: one region), blend half-width [AU]
+    double squashed, nose_th, nose_ph, ts_tail, ts_flank, hp_tail, hp_flank;   // nose-squashed surfaces
     double shell_K0[COSMICA_MAX_SHELLS], shell_tilt_deg[COSMICA_MAX_SHELLS];
     int32_t precision, pad;
     // derived on the device

@@ -67,6 +67,18 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Outside the outer boundary: r >= R_out, or outside the squashed outer spheroid.
+static bool outside_host(const cosmica_params &p, double r, double th, double ph)
+{
+    if (!p.squashed) return r >= p.R_out_AU;
+    const double mu = std::sin(th) * std::sin(p.nose_th_rad) * std::cos(ph - p.nose_ph_rad) +
+                      std::cos(th) * std::cos(p.nose_th_rad);
+    const double a = p.R_out_AU * (1.0 + p.hp_tail_ratio) / 2.0, b = p.R_out_AU * p.hp_flank_ratio;
+    const double c = p.R_out_AU * (p.hp_tail_ratio - 1.0) / 2.0;
+    const double xa = r * mu + c;
+    return xa * xa / (a * a) + r * r * (1.0 - mu * mu) / (b * b) >= 1.0;
+}
+
 cosmica_status check_params(const cosmica_params *p)
 {
     if (!p) return fail(COSMICA_ERR_INVALID, "params is NULL");
@@ -76,8 +88,14 @@ cosmica_status check_params(const cosmica_params *p)
         return fail(COSMICA_ERR_INVALID, "params.version %u != %u", p->version, COSMICA_ABI_VERSION);
     auto pos = [](double x) { return std::isfinite(x) && x > 0.0; };
     if (!pos(p->K0)) return fail(COSMICA_ERR_INVALID, "K0 must be > 0");
-    if (!(p->r_in_AU > 0.0 && p->r0_AU >= p->r_in_AU && p->R_out_AU > p->r0_AU))
-        return fail(COSMICA_ERR_INVALID, "need 0 < r_in <= r0 < R_out");
+    if (p->squashed != 0 && p->squashed != 1) return fail(COSMICA_ERR_INVALID, "squashed must be 0 or 1");
+    if (p->squashed && !(pos(p->ts_tail_ratio) && pos(p->ts_flank_ratio) && pos(p->hp_tail_ratio) &&
+                         pos(p->hp_flank_ratio) && std::isfinite(p->nose_th_rad) && std::isfinite(p->nose_ph_rad)))
+        return fail(COSMICA_ERR_INVALID, "squashed heliosphere needs positive tail/flank ratios and a nose direction");
+    if (!(p->r_in_AU > 0.0 && p->r0_AU >= p->r_in_AU && pos(p->R_out_AU)))
+        return fail(COSMICA_ERR_INVALID, "need 0 < r_in <= r0 and R_out > 0");
+    if (outside_host(*p, p->r0_AU, p->th0_rad, p->ph0_rad))
+        return fail(COSMICA_ERR_INVALID, "the start point lies outside the outer boundary");
     if (!(p->th0_rad > 0.0 && p->th0_rad < kPi)) return fail(COSMICA_ERR_INVALID, "th0 must lie in (0, pi)");
     if (!(p->dt_fixed_day > 0.0) && !(pos(p->dt_max_day) && pos(p->dt_min_day) && p->dt_min_day <= p->dt_max_day))
         return fail(COSMICA_ERR_INVALID, "need dt_fixed > 0 or 0 < dt_min <= dt_max");
@@ -118,7 +136,8 @@ cosmica_status check_params(const cosmica_params *p)
 
 bool valid_start(const cosmica_params &p, double r0, double th0, double ph0)
 {
-    return std::isfinite(r0) && r0 >= p.r_in_AU && r0 < p.R_out_AU && th0 > 0.0 && th0 < kPi && std::isfinite(ph0);
+    return std::isfinite(r0) && r0 >= p.r_in_AU && th0 > 0.0 && th0 < kPi && std::isfinite(ph0) &&
+           !outside_host(p, r0, th0, ph0);
 }
 
 cosmica_status check_species(const cosmica_species *s)
@@ -143,6 +162,10 @@ DevParams to_dev(const cosmica_params &p)
     d.dlat_deg = p.dlat_deg; d.dts = p.dts_AU; d.dcs_min_deg = p.dcs_min_deg; d.rot_period = p.rot_period_day;
     d.r0 = p.r0_AU; d.th0 = p.th0_rad; d.ph0 = p.ph0_rad; d.max_steps = (double)p.max_steps;
     d.formulation = (double)p.formulation;
+    d.squashed = p.squashed ? 1.0 : 0.0;
+    d.nose_th = p.nose_th_rad; d.nose_ph = p.nose_ph_rad;
+    d.ts_tail = p.ts_tail_ratio; d.ts_flank = p.ts_flank_ratio;
+    d.hp_tail = p.hp_tail_ratio; d.hp_flank = p.hp_flank_ratio;
     d.n_shells = (double)p.n_shells;
     d.shell_w = p.shell_blend_AU;
     for (uint32_t k = 0; k < COSMICA_MAX_SHELLS; ++k) {
@@ -395,6 +418,10 @@ extern "C" void cosmica_params_default(cosmica_params *p)
     p->precision = COSMICA_PREC_FP64;
     p->n_shells = 0;
     p->shell_blend_AU = 0.5;
+    p->squashed = 0;
+    p->nose_th_rad = kPi / 2.0;
+    p->nose_ph_rad = 0.0;
+    p->ts_tail_ratio = p->ts_flank_ratio = p->hp_tail_ratio = p->hp_flank_ratio = 1.0;
 }
 
 static cosmica_status upload_params(const cosmica_params *ps, uint32_t n, DevParams **out)
@@ -495,7 +522,7 @@ static cosmica_status propagate_items(cosmica_model *m, const cosmica_species *s
     if (m->p.precision == COSMICA_PREC_FP64) {
         e = launch_propagate_fp64(a, s);
     } else {
-        const MixedVariant v{m->p.precision, m->p.formulation == 1, m->p.n_shells > 0};
+        const MixedVariant v{m->p.precision, m->p.formulation == 1, m->p.n_shells > 0 || m->p.squashed != 0};
         e = launch_propagate_mixed(a, v, shape_for(v, nullptr, total), s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
@@ -725,11 +752,11 @@ struct cosmica_batch {
     std::vector<cosmica_params> params;
     std::vector<cosmica_species> species;
     int precision = 0;
-    bool shells = false;       // some parameter set has radial shells
+    bool extended = false;     // some parameter set has radial shells or a squashed heliosphere
     DevParams *d_prm = nullptr;
     DevSpecies *d_spc = nullptr;
     Tables tab;
-    MixedVariant variant() const { return MixedVariant{precision, params[0].formulation == 1, shells}; }
+    MixedVariant variant() const { return MixedVariant{precision, params[0].formulation == 1, extended}; }
     ExitStage exit_stage;
     DevBuf spec_items, lis_buf;
     Staging spec_stage, lis_stage;
@@ -763,7 +790,8 @@ extern "C" cosmica_status cosmica_batch_create(const cosmica_params *params, uin
     b->params.assign(params, params + n_params);
     b->species.assign(species, species + n_species);
     b->precision = params[0].precision;
-    for (uint32_t i = 0; i < n_params; ++i) b->shells = b->shells || params[i].n_shells > 0;
+    for (uint32_t i = 0; i < n_params; ++i)
+        b->extended = b->extended || params[i].n_shells > 0 || params[i].squashed != 0;
     cosmica_status st = upload_params(params, n_params, &b->d_prm);
     if (st == COSMICA_OK) {
         std::vector<DevSpecies> hs(n_species);
@@ -924,7 +952,7 @@ extern "C" cosmica_status cosmica_batch_spectrum(cosmica_batch *b, const cosmica
 // Tuned shapes are cached per (device, configuration class): the precision,
 // whether the sets have a drift / a termination shock, the particle count to
 // within a factor of two (it sets the particles per lane, hence the tail), and
-// the kernel variant (energy form, radial shells).
+// the kernel variant (energy form, radial shells or squashed heliosphere).
 namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int>, std::pair<cosmica_tuning, double>> g_tune_cache;
@@ -946,7 +974,7 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
     int size_class = 0;
     while ((n_all >> size_class) > 1) ++size_class;
     // the kernel variant (energy form, shells) has its own registers, hence its own best shape
-    const int variant = (b->params[0].formulation == 1 ? 1 : 0) | (b->shells ? 2 : 0);
+    const int variant = (b->params[0].formulation == 1 ? 1 : 0) | (b->extended ? 2 : 0);
     const auto key = std::make_tuple(dev, b->precision, drift, ts, size_class, variant);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);

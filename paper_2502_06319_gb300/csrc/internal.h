@@ -83,7 +83,7 @@ cudaError_t launch_propagate_fp64(const LaunchArgs &a, cudaStream_t s);
 struct MixedVariant {
     int acc;        // COSMICA_PREC_MIXED or COSMICA_PREC_MIXED_F64ACC
     bool energy;    // energy formulation (Eq. 1) instead of the momentum form
-    bool shells;    // some parameter set of the launch has radial shells
+    bool extended;  // some parameter set of the launch has radial shells or a squashed heliosphere
 };
 cudaError_t launch_propagate_mixed(const LaunchArgs &a, MixedVariant v, PersistentShape shape, cudaStream_t s);
 int mixed_max_blocks_per_sm(MixedVariant v, unsigned block, bool compact);

@@ -68,6 +68,24 @@ __global__ void k_derive(DevParams *prm, uint32_t n)
         f.sh_K0[k] = (float)p.shell_K0[k];
         f.sh_alpha[k] = (float)(p.shell_tilt_deg[k] * kDeg);
     }
+    const bool sq = p.squashed != 0.0;
+    f.sq = sq ? 1.0f : 0.0f;
+    f.nose_ph = (float)(p.nose_ph - kTwoPi * floor(p.nose_ph / kTwoPi));
+    f.sin_nth = (float)sin(p.nose_th);
+    f.cos_nth = (float)cos(p.nose_th);
+    {
+        // shock spheroid with unit nose distance (scaled by ts_R), outer spheroid in AU
+        const double a = (1.0 + p.ts_tail) / 2.0, b = p.ts_flank, c = (p.ts_tail - 1.0) / 2.0;
+        f.ts_R = (float)p.R_ts;
+        f.ts_c = (float)c;
+        f.ts_ia2 = (float)(1.0 / (a * a));
+        f.ts_ib2 = (float)(1.0 / (b * b));
+        f.ts_C = (float)(c * c / (a * a) - 1.0);
+        const double A = p.R_out * (1.0 + p.hp_tail) / 2.0, B = p.R_out * p.hp_flank;
+        f.hp_c = (float)(p.R_out * (p.hp_tail - 1.0) / 2.0);
+        f.hp_ia2 = (float)(1.0 / (A * A));
+        f.hp_ib2 = (float)(1.0 / (B * B));
+    }
 }
 
 __global__ void __launch_bounds__(128) k_propagate_fp64(const DevParams *__restrict__ prm,

@@ -50,7 +50,7 @@ __device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t q, 
 
 // One Euler-Maruyama step (Eq. 3, Eq. 6) of an active lane; true when the path ended
 // (exit record written).
-template <int ACC, bool EN, bool SH>
+template <int ACC, bool EN, bool EXT>
 __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, EnergyAcc<ACC, EN> &en,
                                      unsigned long long &my_steps)
 {
@@ -66,7 +66,7 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
     } else {
         lnP = x.flnP();
     }
-    m32::eval<SH>(q, L.M2, L.sq, x.fr(), x.fth(), x.fph(), lnP, c);
+    m32::eval<EXT>(q, L.M2, L.sq, x.fr(), x.fth(), x.fph(), lnP, c);
     const float sdt = sqrtf(c.dt);
     const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
     const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);
@@ -85,7 +85,8 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
 
     int status = COSMICA_PATH_RUNNING;
     if (!x.finite()) status = COSMICA_PATH_NONFINITE;
-    else if (x.exited()) status = COSMICA_PATH_EXIT;
+    else if ((EXT && q.sq != 0.0f) ? m32::outside_squashed(q, x.fr(), x.fth(), x.fph()) : x.exited())
+        status = COSMICA_PATH_EXIT;
     else if (L.k >= L.max_steps) status = COSMICA_PATH_STEP_LIMIT;
     if (status == COSMICA_PATH_RUNNING) return false;
     x.write(a.out, L.g);
@@ -111,7 +112,7 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
 // they need, repacked through shared memory into the block's lowest lanes, so that
 // issued warp instructions keep carrying full lanes while the long tail of exit
 // times plays out.  Both phases share one step site (one copy of the step code).
-template <int ACC, bool COMPACT, bool EN, bool SH>
+template <int ACC, bool COMPACT, bool EN, bool EXT>
 __global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a, uint32_t period)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a, uint32_t 
             // an idle warp goes straight to the next checkpoint
             tick = __any_sync(0xffffffffu, active) ? (tick + 1 == period ? 0 : tick + 1) : 0;
         }
-        if (active && step<ACC, EN, SH>(a, L, x, en, my_steps)) active = false;
+        if (active && step<ACC, EN, EXT>(a, L, x, en, my_steps)) active = false;
     }
     if (a.steps_total) {
         for (int o = 16; o > 0; o >>= 1) my_steps += __shfl_down_sync(0xffffffffu, my_steps, o);
@@ -226,14 +227,14 @@ __global__ void k_debug_eval32(const DevParams *__restrict__ prm, const DevSpeci
 template <int ACC, bool EN>
 static size_t pack_bytes(unsigned block) { return (size_t)block * sizeof(Packed<ACC, EN>); }
 
-// Call fn(acc, compact, energy, shells) with each flag as a compile-time constant.
+// Call fn(acc, compact, energy, extended) with each flag as a compile-time constant.
 template <class Fn>
 static void visit_variant(MixedVariant v, bool compact, Fn &&fn)
 {
     auto on_acc = [&](auto A) {
         auto on_compact = [&](auto C) {
             auto on_energy = [&](auto E) {
-                if (v.shells) fn(A, C, E, std::true_type{});
+                if (v.extended) fn(A, C, E, std::true_type{});
                 else fn(A, C, E, std::false_type{});
             };
             if (v.energy) on_energy(std::true_type{});

@@ -74,9 +74,47 @@ __device__ __forceinline__ void shell_weights(const F32Params &q, float r, int &
 
 // Coefficients at (r, th, ph, lnP).  q: FP32 constants of the heliosphere.
 // M2 = (A/|Z| m0)^2, sq = sign of the charge.
-// SH: the parameter sets of the launch may have radial shells (compile-time, so
-// that single-region launches carry none of the shell code or its registers).
-template <bool SH>
+// Nose-squashed spheroid (Sec. II.B) in FP32: distance R from the Sun along
+// the direction mu and dR/dmu; ia2 = 1/a^2, ib2 = 1/b^2, c = centre offset,
+// C = c^2/a^2 - 1 (the positive root of A R^2 + 2 B R + C = 0).
+__device__ __forceinline__ float spheroid_radius(float ia2, float ib2, float c, float C, float mu, float &dR_dmu)
+{
+    const float mu2 = mu * mu;
+    const float A = fmaf(mu2, ia2 - ib2, ib2);
+    const float B = mu * c * ia2;
+    const float Rm = __fdividef(-C, B + sqrtf(fmaf(B, B, -A * C)));
+    dR_dmu = -__fdividef(Rm * fmaf(Rm * mu, ia2 - ib2, c * ia2), fmaf(A, Rm, B));
+    return Rm;
+}
+
+// cos of the angle between the direction (th, ph) and the nose, with its derivatives
+__device__ __forceinline__ float nose_mu(const F32Params &q, float sn, float cs, float ph, float &dmu_dth,
+                                         float &dmu_dph)
+{
+    float d = ph - q.nose_ph;                      // nose_ph in [0, 2 pi): d in (-2 pi, 2 pi)
+    d = (d > kPiF) ? d - kTwoPiF : ((d < -kPiF) ? d + kTwoPiF : d);
+    float sd, cd;
+    __sincosf(d, &sd, &cd);
+    dmu_dth = fmaf(cs * q.sin_nth, cd, -sn * q.cos_nth);
+    dmu_dph = -sn * q.sin_nth * sd;
+    return fmaf(sn * q.sin_nth, cd, cs * q.cos_nth);
+}
+
+// Outside the squashed outer spheroid (FP32; the spherical boundary keeps its exact test).
+__device__ __forceinline__ bool outside_squashed(const F32Params &q, float r, float th, float ph)
+{
+    float sn, cs, dth, dph;
+    __sincosf(th, &sn, &cs);
+    const float mu = nose_mu(q, sn, cs, ph, dth, dph);
+    const float xa = fmaf(r, mu, q.hp_c);
+    const float rp2 = r * r * fmaf(-mu, mu, 1.0f);
+    return fmaf(xa * xa, q.hp_ia2, rp2 * q.hp_ib2) >= 1.0f;
+}
+
+// EXT: the parameter sets of the launch may have radial shells or a squashed
+// heliosphere (compile-time, so that launches of the basic model carry none of
+// that code or its registers).
+template <bool EXT>
 __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, float r, float th, float ph,
                                      float lnP, Drift &o, float *dbg = nullptr)
 {
@@ -103,17 +141,30 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
     const float iq = __fdividef(1.0f, fmaf(Gam, Gam, 1.0f));
     const float dGam_dth = Gam * fmaf(-dV, inv_V, cot);
 
-    // termination shock factor (uniform branch: no shock in the parameter set)
-    float g = 1.0f, dg = 0.0f;
+    // termination shock factor (uniform branch: no shock in the parameter set); a
+    // squashed shock sits at its spheroid's distance along the point's direction
+    float g = 1.0f, dg = 0.0f, dg_dth = 0.0f, dg_dph = 0.0f;
+    const bool squashed = EXT && q.sq != 0.0f;
     if (q.ts_drop != 0.0f) {
-        const float st = half_one_plus_tanh((r - q.R_ts) * q.inv_dts);
+        float Rts = q.R_ts, dR_dmu = 0.0f, dmu_dth = 0.0f, dmu_dph = 0.0f;
+        if (squashed) {
+            const float mu = nose_mu(q, sn, cs, ph, dmu_dth, dmu_dph);
+            Rts = q.ts_R * spheroid_radius(q.ts_ia2, q.ts_ib2, q.ts_c, q.ts_C, mu, dR_dmu);
+            dR_dmu *= q.ts_R;
+        }
+        const float st = half_one_plus_tanh((r - Rts) * q.inv_dts);
         g = fmaf(-q.ts_drop, st, 1.0f);
-        dg = -q.ts_drop * 2.0f * st * (1.0f - st) * q.inv_dts;
+        const float w = q.ts_drop * 2.0f * st * (1.0f - st) * q.inv_dts;
+        dg = -w;
+        if (squashed) {
+            dg_dth = w * dR_dmu * dmu_dth;
+            dg_dph = w * dR_dmu * dmu_dph;
+        }
     }
 
     // radial shells: K0 and the sheet tilt of the shell holding r (the single-region
     // tilt is read where the sheet needs it, so that it is not live before)
-    const bool shells = SH && q.n_sh != 0.0f;
+    const bool shells = EXT && q.n_sh != 0.0f;
     float K0 = q.K0, dK0 = 0.0f, sh_ta = 0.0f, sh_ta2 = 0.0f, dta = 0.0f;
     if (shells) {
         int a, b;
@@ -148,10 +199,18 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
     const float dKrp = erm1 * fmaf(dKpar, sc, Kpar * dsc_dr);
 
     // Ito drift (1/sqrt g) d_j (sqrt g K^ij)
-    const float Ar = fmaf(2.0f * Krr, inv_r, dKrr);
-    const float Ath = Ktt * cot * inv_r * inv_r;
+    float Ar = fmaf(2.0f * Krr, inv_r, dKrr);
+    float Ath = Ktt * cot * inv_r * inv_r;
     const float inv_rs = inv_r * inv_sn;
-    const float Aph = fmaf(Krp, inv_r, dKrp) * inv_rs;
+    float Aph = fmaf(Krp, inv_r, dKrp) * inv_rs;
+    if (squashed) {
+        // K depends on th and ph through the squashed shock: d_th K_thth / r^2,
+        // d_ph K_rph / (r sin th) and d_ph K_phph / (r sin th)^2
+        const float dKpar_th = Kb * dg_dth, dKpar_ph = Kb * dg_dph;
+        Ath = fmaf(q.et * dKpar_th, inv_r * inv_r, Ath);
+        Ar = fmaf(erm1 * dKpar_ph * sc, inv_rs, Ar);
+        Aph = fmaf(dKpar_ph * fmaf(q.er, iq, G2 * iq), inv_rs * inv_rs, Aph);
+    }
 
     // Cholesky factor of 2K
     const float rK = rsqrtf(Krr);

@@ -98,6 +98,48 @@ __device__ __forceinline__ void shell_value(const DevParams &p, const double *v,
     *dval = (v[lo + 1] - v[lo]) * dS;
 }
 
+// Nose-squashed heliosphere (Sec. II.B): surfaces are spheroids about the nose
+// axis with the Sun on the axis (nose distance R, tail R t, flank semi-axis R f).
+// mu = cosine of the angle between the point's direction and the nose.
+__device__ __forceinline__ double nose_mu(const DevParams &p, double th, double ph, double *dmu_dth,
+                                          double *dmu_dph)
+{
+    double st, ct, sn, cn, sd, cd;
+    dm::sincos(th, &st, &ct);
+    dm::sincos(p.nose_th, &sn, &cn);
+    dm::sincos(ph - p.nose_ph, &sd, &cd);
+    if (dmu_dth) *dmu_dth = ct * sn * cd - st * cn;
+    if (dmu_dph) *dmu_dph = -st * sn * sd;
+    return st * sn * cd + ct * cn;
+}
+
+// Distance from the Sun to the spheroid along mu and dR/dmu (positive root of
+// A R^2 + 2 B R + C = 0, in the cancellation-free form R = -C / (B + sqrt(B^2 - A C))).
+__device__ __forceinline__ double spheroid_radius(double R, double t, double f, double mu, double *dR_dmu)
+{
+    const double a = R * (1.0 + t) / 2.0, b = R * f, c = R * (t - 1.0) / 2.0;
+    const double A = mu * mu / (a * a) + (1.0 - mu * mu) / (b * b);
+    const double B = mu * c / (a * a);
+    const double C = c * c / (a * a) - 1.0;
+    const double Rm = -C / (B + sqrt(B * B - A * C));
+    if (dR_dmu) {
+        const double dF_dmu = Rm * Rm * mu * (1.0 / (a * a) - 1.0 / (b * b)) + Rm * c / (a * a);
+        *dR_dmu = -dF_dmu / (A * Rm + B);
+    }
+    return Rm;
+}
+
+// Outer boundary: r >= R_out, or outside the squashed outer spheroid.
+__device__ __forceinline__ bool outside(const DevParams &p, double r, double th, double ph)
+{
+    if (p.squashed == 0.0) return r >= p.R_out;
+    const double mu = nose_mu(p, th, ph, nullptr, nullptr);
+    const double a = p.R_out * (1.0 + p.hp_tail) / 2.0, b = p.R_out * p.hp_flank;
+    const double c = p.R_out * (p.hp_tail - 1.0) / 2.0;
+    const double xa = r * mu + c;
+    return xa * xa / (a * a) + r * r * (1.0 - mu * mu) / (b * b) >= 1.0;
+}
+
 __device__ __forceinline__ void eval(const DevParams &p, const DevSpecies &sp, double r, double th,
                                      double ph, double lnP, Coef &c)
 {
@@ -114,8 +156,18 @@ __device__ __forceinline__ void eval(const DevParams &p, const DevSpecies &sp, d
 
     wind(p, th, &c.V, &c.dV_dth);
 
-    double g, dg_dr;
-    if (p.R_ts > 0.0) {
+    double g, dg_dr, dg_dth = 0.0, dg_dph = 0.0;
+    if (p.R_ts > 0.0 && p.squashed != 0.0) {
+        double dmu_dth, dmu_dph, dR_dmu;
+        const double mu = nose_mu(p, th, ph, &dmu_dth, &dmu_dph);
+        const double Rts = spheroid_radius(p.R_ts, p.ts_tail, p.ts_flank, mu, &dR_dmu);
+        const double t = dm::tanh((r - Rts) / p.dts);
+        const double sech2 = 1.0 - t * t;
+        g = 1.0 - (1.0 - p.ts_f) * 0.5 * (1.0 + t);
+        dg_dr = -(1.0 - p.ts_f) * 0.5 * sech2 / p.dts;
+        dg_dth = (1.0 - p.ts_f) * 0.5 * sech2 / p.dts * dR_dmu * dmu_dth;
+        dg_dph = (1.0 - p.ts_f) * 0.5 * sech2 / p.dts * dR_dmu * dmu_dph;
+    } else if (p.R_ts > 0.0) {
         const double t = dm::tanh((r - p.R_ts) / p.dts);
         g = 1.0 - (1.0 - p.ts_f) * 0.5 * (1.0 + t);
         dg_dr = -(1.0 - p.ts_f) * 0.5 * (1.0 - t * t) / p.dts;
@@ -134,19 +186,22 @@ __device__ __forceinline__ void eval(const DevParams &p, const DevSpecies &sp, d
     const double Kpar = Kbase * g;
     double dKpar_dr = Kbase * dg_dr;
     if (p.n_shells > 0.0) dKpar_dr = dKpar_dr + dK0_dr * beta * P * g;
-    const double dKpar_dth = 0.0;
+    const double dKpar_dth = Kbase * dg_dth;
+    const double dKpar_dph = Kbase * dg_dph;
     c.Kpar = Kpar;
 
     // tensor components and the derivatives the drift needs; K_rth = K_thph = 0
     double K00, K11, K22, K02 = 0.0, K01 = 0.0, K12 = 0.0;
     double Kr00, Kr02 = 0.0, Kr01 = 0.0;
     double Kt11, Kt01 = 0.0, Kt12 = 0.0;
+    double Kp02 = 0.0, Kp12 = 0.0, Kp22;   // d/dph (a squashed shock makes K depend on ph)
     c.Gam = 0.0;
     c.dGam_dth = 0.0;
     if (p.isotropic != 0.0) {
         K00 = Kpar; K11 = Kpar; K22 = Kpar;
         Kr00 = dKpar_dr;
         Kt11 = dKpar_dth;
+        Kp22 = dKpar_dph;
     } else {
         const double Omega = kTwoPi / p.rot_period;
         const double Gam = Omega * r * sin_th / c.V;
@@ -172,6 +227,9 @@ __device__ __forceinline__ void eval(const DevParams &p, const DevSpecies &sp, d
         Kr00 = dKpar_dr * c2 + Kpar * dc2_dr + dKpr_dr * s2 + Kpr * ds2_dr;
         Kr02 = (dKpr_dr - dKpar_dr) * sc + (Kpr - Kpar) * dsc_dr;
         Kt11 = dKpt_dth;
+        const double dKpr_dph = er * dKpar_dph;
+        Kp02 = (dKpr_dph - dKpar_dph) * sc;
+        Kp22 = dKpar_dph * s2 + dKpr_dph * c2;
     }
     c.K00 = K00; c.K11 = K11; c.K22 = K22; c.K02 = K02;
     c.dKrr_dr = Kr00; c.dKrp_dr = Kr02;
@@ -180,6 +238,11 @@ __device__ __forceinline__ void eval(const DevParams &p, const DevSpecies &sp, d
     c.Ar = Kr00 + 2.0 * K00 / r + Kt01 / r + K01 * cot_th / r;
     c.Ath = (Kt11 + K11 * cot_th) / (r * r) + Kr01 / r + K01 / (r * r);
     c.Aph = (Kr02 + K02 / r) / (r * sin_th) + Kt12 / (r * r * sin_th);
+    if (p.squashed != 0.0) {
+        c.Ar = c.Ar + Kp02 / (r * sin_th);
+        c.Ath = c.Ath + Kp12 / (r * r * sin_th);
+        c.Aph = c.Aph + Kp22 / (r * r * sin_th * sin_th);
+    }
 
     // lower Cholesky factor of 2K
     {
@@ -365,7 +428,7 @@ __device__ __forceinline__ void em_step(const DevParams &p, const DevSpecies &sp
     x.k = x.k + 1u;
     if (!(isfinite(x.r) && isfinite(x.th) && isfinite(x.ph) && isfinite(x.lnP) && isfinite(x.s))) {
         x.status = COSMICA_PATH_NONFINITE;
-    } else if (x.r >= p.R_out) {
+    } else if (outside(p, x.r, x.th, x.ph)) {
         x.status = COSMICA_PATH_EXIT;
     } else if ((double)x.k >= p.max_steps) {
         x.status = COSMICA_PATH_STEP_LIMIT;

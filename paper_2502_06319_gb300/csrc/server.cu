@@ -432,8 +432,8 @@ extern "C" cosmica_status cosmica_server_submit(cosmica_server *s, const cosmica
     if (stt != COSMICA_OK) return stt;
     if (q->params.precision != s->precision) return fail(COSMICA_ERR_INVALID, "request precision differs from the server's");
     if (q->params.formulation != 0) return fail(COSMICA_ERR_INVALID, "the server runs the momentum form only");
-    if (q->params.n_shells != 0)
-        return fail(COSMICA_ERR_INVALID, "the server runs single-region heliospheres only (n_shells = 0)");
+    if (q->params.n_shells != 0 || q->params.squashed != 0)
+        return fail(COSMICA_ERR_INVALID, "the server runs the basic heliosphere only (no shells, not squashed)");
     if (q->n_energies == 0 || q->n_energies > kMaxEnergies || !q->T_GeVn || !q->n_per_energy)
         return fail(COSMICA_ERR_INVALID, "need 1..%u energies with T and counts", kMaxEnergies);
     if (!(q->bins.P_min_GV > 0.0 && q->bins.P_max_GV > q->bins.P_min_GV && q->bins.nbins >= 1 &&

@@ -34,6 +34,7 @@ PARAM_FIELDS = (
     "V_const_kms", "eps_adv", "eps_diff", "dt_min", "dlat_deg", "dts_AU",
     "dcs_min_deg", "rot_period_day", "r0", "th0", "ph0", "formulation",
     "n_shells", "shell_blend_AU",
+    "squashed", "nose_th", "nose_ph", "ts_tail", "ts_flank", "hp_tail", "hp_flank",
 )
 MAX_SHELLS = 16
 SHELL_ARRAYS = ("shell_K0", "shell_tilt_deg")   # per-shell tables (lists of up to 16 values)
@@ -72,6 +73,13 @@ DEFAULT_PARAMS: Dict[str, float] = {
     "formulation": 0.0,     # 0: momentum form (Eq. 5-6); 1: energy form with loss weight (Eq. 1, Eq. 4)
     "n_shells": 0.0,        # radial shells of the inner heliosphere (0: one region)
     "shell_blend_AU": 0.5,  # half-width of the blend across each interior shell edge
+    "squashed": 0.0,        # 1: shock and outer boundary are spheroids squashed toward the nose
+    "nose_th": math.pi / 2.0,   # nose direction (colatitude, longitude) [rad]
+    "nose_ph": 0.0,
+    "ts_tail": 1.0,         # shock: tail distance / nose distance (R_ts)
+    "ts_flank": 1.0,        # shock: flank semi-axis / nose distance
+    "hp_tail": 1.0,         # outer boundary: the same ratios (R_out at the nose)
+    "hp_flank": 1.0,
     "shell_K0": (),         # K0 of each shell [AU^2/day], innermost first
     "shell_tilt_deg": (),   # current-sheet tilt of each shell [deg]
 }
@@ -151,11 +159,22 @@ def config3_param_sets(seed: int = 20250210, n_sets: int = 64) -> List[Dict[str,
     return out
 
 
+# Nose-squashed heliosphere (Sec. II.B): shock 85 AU at the nose, 1.35x at the tail, 1.15x
+# on the flanks; outer boundary 122 AU at the nose, 1.6x / 1.25x; nose 5 deg south of the
+# ecliptic.  A synthetic shape of the right proportions (HelMod's fitted surfaces are not
+# available).
+SQUASHED = {"squashed": 1.0, "nose_th": math.pi / 2.0 + math.radians(5.0), "nose_ph": math.radians(255.0),
+            "ts_tail": 1.35, "ts_flank": 1.15, "hp_tail": 1.6, "hp_flank": 1.25}
+
+
 def config3(seed: int = 20250210, n_sets: int = 64, n_e: int = 30,
-            n_lo: int = 1_000, n_hi: int = 50_000, scale: float = 1.0) -> List[Job]:
+            n_lo: int = 1_000, n_hi: int = 50_000, scale: float = 1.0, geometry=None) -> List[Job]:
     """Batched workload: 64 parameter sets x {proton, He-4, electron} x 30 energies,
-    uneven log-uniform counts in [n_lo, n_hi] (scaled by `scale`)."""
+    uneven log-uniform counts in [n_lo, n_hi] (scaled by `scale`); `geometry` overrides
+    the boundary shape (e.g. SQUASHED)."""
     sets = config3_param_sets(seed, n_sets)
+    if geometry:
+        sets = [dict(p, **{k: float(v) for k, v in geometry.items()}) for p in sets]
     rng = np.random.default_rng(seed + 1)
     T = logspace(0.1, 100.0, n_e)
     jobs = []
