@@ -7,6 +7,7 @@
 // deterministic elementary functions) so that host and device never disagree
 // on a constant.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 
 #include "cosmica.h"
@@ -70,6 +71,21 @@ struct DevParams {
     double B0;                 // nT, |B|(1 AU, equator) = B1AU
     F32Params f;
 };
+
+// Read-only view of one parameter set's FP32 block in a table whose consecutive
+// fields lie `stride` floats apart: stride 1 reads one F32Params in place; a
+// batch of n sets uses a field-major table (field f of set i at f * n + i), so
+// that the lanes of a warp reading one field of different sets touch adjacent
+// words of one or two cache lines instead of one line per set.
+struct P32 {
+    const float *__restrict__ p;   // field 0 of the set
+    uint32_t stride;
+    __device__ __forceinline__ float at(uint32_t field) const { return __ldg(p + field * stride); }
+};
+#define P32F(q, m) ((q).at((uint32_t)(offsetof(F32Params, m) / sizeof(float))))
+#define P32A(q, m, k) ((q).at((uint32_t)(offsetof(F32Params, m) / sizeof(float)) + (uint32_t)(k)))
+constexpr uint32_t kF32Fields = sizeof(F32Params) / sizeof(float);
+static_assert(sizeof(F32Params) % sizeof(float) == 0, "F32Params holds floats only");
 
 struct DevSpecies {
     double A, Z, m0;           // as doubles, the FP64 step's arithmetic type

@@ -368,6 +368,7 @@ using namespace cosmica::host;
 struct cosmica_model {
     cosmica_params p;
     DevParams *d_prm = nullptr;
+    const float *d_f32 = nullptr;   // field-major FP32 block (inside the d_prm allocation)
     DevBuf spc;                 // DevSpecies[1] + spectrum items
     Staging spc_stage;
     Tables tab;
@@ -424,20 +425,28 @@ extern "C" void cosmica_params_default(cosmica_params *p)
     p->ts_tail_ratio = p->ts_flank_ratio = p->hp_tail_ratio = p->hp_flank_ratio = 1.0;
 }
 
-static cosmica_status upload_params(const cosmica_params *ps, uint32_t n, DevParams **out)
+// Upload n parameter sets, derive their constants on the device, and lay out
+// their FP32 blocks field-major right after them in the same allocation
+// (*f32: field f of set i at f * n + i), the layout the mixed kernels read.
+static cosmica_status upload_params(const cosmica_params *ps, uint32_t n, DevParams **out, const float **f32)
 {
     std::vector<DevParams> h(n);
     for (uint32_t i = 0; i < n; ++i) h[i] = to_dev(ps[i]);
-    DevParams *d = nullptr;
-    CK(cudaMalloc(&d, n * sizeof(DevParams)), "cudaMalloc(params)");
-    cudaError_t e = cudaMemcpy(d, h.data(), n * sizeof(DevParams), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = launch_derive(d, n, 0);
+    const size_t b_prm = align_up(n * sizeof(DevParams), 256);
+    char *d = nullptr;
+    CK(cudaMalloc(&d, b_prm + (size_t)n * kF32Fields * sizeof(float)), "cudaMalloc(params)");
+    DevParams *dp = reinterpret_cast<DevParams *>(d);
+    float *table = reinterpret_cast<float *>(d + b_prm);
+    cudaError_t e = cudaMemcpy(dp, h.data(), n * sizeof(DevParams), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_derive(dp, n, 0);
+    if (e == cudaSuccess) e = launch_f32_table(dp, n, table, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(d);
         return cuda_fail(e, "deriving parameter constants");
     }
-    *out = d;
+    *out = dp;
+    *f32 = table;
     return COSMICA_OK;
 }
 
@@ -450,7 +459,7 @@ extern "C" cosmica_status cosmica_model_create(const cosmica_params *params, cos
     cosmica_model *m = new (std::nothrow) cosmica_model();
     if (!m) return fail(COSMICA_ERR_OOM, "host allocation of the model");
     m->p = *params;
-    st = upload_params(params, 1, &m->d_prm);
+    st = upload_params(params, 1, &m->d_prm, &m->d_f32);
     if (st != COSMICA_OK) {
         delete m;
         return st;
@@ -517,7 +526,7 @@ static cosmica_status propagate_items(cosmica_model *m, const cosmica_species *s
     }
     CK(cudaMemsetAsync(m->tab.counters, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
     LaunchArgs a{m->d_prm, d_sp, m->tab.items, m->tab.prefix, m->tab.n_items, total, ex,
-                 m->tab.counters + 1, m->tab.counters, m->tab.qitem, m->tab.qprefix};
+                 m->tab.counters + 1, m->tab.counters, m->tab.qitem, m->tab.qprefix, m->d_f32, 1u};
     cudaError_t e;
     if (m->p.precision == COSMICA_PREC_FP64) {
         e = launch_propagate_fp64(a, s);
@@ -754,6 +763,7 @@ struct cosmica_batch {
     int precision = 0;
     bool extended = false;     // some parameter set has radial shells or a squashed heliosphere
     DevParams *d_prm = nullptr;
+    const float *d_f32 = nullptr;   // field-major FP32 blocks (inside the d_prm allocation)
     DevSpecies *d_spc = nullptr;
     Tables tab;
     MixedVariant variant() const { return MixedVariant{precision, params[0].formulation == 1, extended}; }
@@ -762,7 +772,25 @@ struct cosmica_batch {
     Staging spec_stage, lis_stage;
     // CUDA graph of [memset counters, persistent kernel] for repeated runs
     cudaGraphExec_t gexec = nullptr;
-    std::tuple<uint64_t, uint32_t, const void *, const void *, unsigned, unsigned, cudaStream_t, int> gkey{};
+    // every value the captured launch bakes in: a replay is valid only when all are unchanged
+    struct GraphKey {
+        uint64_t total = 0;
+        uint32_t n_items = 0;
+        const void *tables = nullptr;
+        ExitPtrs ex{};
+        PersistentShape shape{};
+        cudaStream_t stream = nullptr;
+        int precision = -1;
+        bool operator==(const GraphKey &o) const
+        {
+            return total == o.total && n_items == o.n_items && tables == o.tables && ex.r == o.ex.r &&
+                   ex.th == o.ex.th && ex.ph == o.ex.ph && ex.lnP == o.ex.lnP && ex.s == o.ex.s &&
+                   ex.steps == o.ex.steps && ex.status == o.ex.status && ex.item == o.ex.item &&
+                   ex.lw == o.ex.lw && shape.block == o.shape.block && shape.grid == o.shape.grid &&
+                   shape.compact_period == o.shape.compact_period && stream == o.stream &&
+                   precision == o.precision;
+        }
+    } gkey;
 };
 
 extern "C" cosmica_status cosmica_batch_create(const cosmica_params *params, uint32_t n_params,
@@ -792,7 +820,7 @@ extern "C" cosmica_status cosmica_batch_create(const cosmica_params *params, uin
     b->precision = params[0].precision;
     for (uint32_t i = 0; i < n_params; ++i)
         b->extended = b->extended || params[i].n_shells > 0 || params[i].squashed != 0;
-    cosmica_status st = upload_params(params, n_params, &b->d_prm);
+    cosmica_status st = upload_params(params, n_params, &b->d_prm, &b->d_f32);
     if (st == COSMICA_OK) {
         std::vector<DevSpecies> hs(n_species);
         for (uint32_t i = 0; i < n_species; ++i) hs[i] = to_dev(species[i]);
@@ -850,7 +878,8 @@ static cosmica_status batch_launch(cosmica_batch *b, uint64_t total, const ExitP
                                    const cosmica_tuning *tuning, cudaStream_t s)
 {
     LaunchArgs a{b->d_prm, b->d_spc, b->tab.items, b->tab.prefix, b->tab.n_items, total, ex,
-                 b->tab.counters + 1, b->tab.counters, b->tab.qitem, b->tab.qprefix};
+                 b->tab.counters + 1, b->tab.counters, b->tab.qitem, b->tab.qprefix, b->d_f32,
+                 (uint32_t)b->params.size()};
     auto direct = [&]() -> cosmica_status {
         CK(cudaMemsetAsync(b->tab.counters, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
         cudaError_t e = (b->precision == COSMICA_PREC_FP64)
@@ -862,9 +891,15 @@ static cosmica_status batch_launch(cosmica_batch *b, uint64_t total, const ExitP
     const bool graph = tuning && tuning->use_graph && s != nullptr;
     if (!graph) return direct();
     const PersistentShape sh = shape_for(b->variant(), tuning, total);
-    auto key = std::make_tuple(total, b->tab.n_items, (const void *)ex.lw, (const void *)b->tab.dev.d, sh.block,
-                               sh.grid * 1024u + sh.compact_period, s, b->precision);
-    if (!b->gexec || b->gkey != key) {
+    cosmica_batch::GraphKey key;
+    key.total = total;
+    key.n_items = b->tab.n_items;
+    key.tables = b->tab.dev.d;
+    key.ex = ex;
+    key.shape = sh;
+    key.stream = s;
+    key.precision = b->precision;
+    if (!b->gexec || !(b->gkey == key)) {
         if (b->gexec) {
             cudaGraphExecDestroy(b->gexec);
             b->gexec = nullptr;

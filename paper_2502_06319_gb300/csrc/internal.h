@@ -23,6 +23,8 @@ struct LaunchArgs {
     unsigned long long *cursor;        // work-queue cursor (persistent kernels)
     const uint32_t *qitem;             // item of each queue slot (null: item order)
     const uint64_t *qprefix;           // prefix sums of particle counts in queue order
+    const float *f32;                  // FP32 blocks of the parameter sets, field-major (P32)
+    uint32_t f32_stride;               // = number of parameter sets in that table
 };
 
 struct PersistentShape {
@@ -76,6 +78,7 @@ int serve_max_blocks_per_sm(int acc, unsigned block);
 void note_launch();
 
 cudaError_t launch_derive(DevParams *prm, uint32_t n, cudaStream_t s);
+cudaError_t launch_f32_table(const DevParams *prm, uint32_t n, float *table, cudaStream_t s);
 cudaError_t launch_propagate_fp64(const LaunchArgs &a, cudaStream_t s);
 
 // mixed precision persistent kernel; acc = COSMICA_PREC_MIXED or COSMICA_PREC_MIXED_F64ACC

@@ -174,6 +174,24 @@ __global__ void k_debug_philox(uint32_t n, const uint32_t *__restrict__ ctr, uin
 // ---------------------------------------------------------------- launchers --
 static inline unsigned grid_for(uint64_t n, unsigned block) { return (unsigned)((n + block - 1) / block); }
 
+// Field-major copy of the FP32 blocks of n parameter sets: field f of set i at f * n + i.
+__global__ void k_f32_table(const DevParams *__restrict__ prm, uint32_t n, float *__restrict__ table)
+{
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n * kF32Fields) return;
+    const uint32_t f = j / n, i = j - f * n;
+    table[j] = reinterpret_cast<const float *>(&prm[i].f)[f];
+}
+
+cudaError_t launch_f32_table(const DevParams *prm, uint32_t n, float *table, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    cudaGetLastError();
+    k_f32_table<<<grid_for(n * kF32Fields, 128), 128, 0, s>>>(prm, n, table);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_derive(DevParams *prm, uint32_t n, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;

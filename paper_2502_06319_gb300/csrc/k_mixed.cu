@@ -33,7 +33,7 @@ __device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t q, 
     const DevItem item = a.items[it];
     const DevParams &p = a.prm[item.param_idx];
     const DevSpecies &sp = a.spc[item.species_idx];
-    L.q = &p.f;
+    L.q = a.f32 + item.param_idx;
     L.M2 = sp.aoz_m0_sq;
     L.sq = sp.sgnq;
     L.pid = item.first_pid + local;
@@ -57,7 +57,7 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
     float z0, z1, z2;
     m32::normals(L.seed, L.pid, L.k, z0, z1, z2);
     m32::Drift c;
-    const F32Params &q = *L.q;
+    const P32 q{L.q, a.f32_stride};
     float lnP;
     if constexpr (EN) {
         // rigidity from the integrated kinetic energy: P = (A/|Z|) sqrt(T (T + 2 m0))
@@ -80,12 +80,12 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
     } else {
         x.add(dr, dth, dph, c.dlnP * c.dt, c.dt);
     }
-    x.boundaries(q.r_in);
+    x.boundaries(P32F(q, r_in));
     L.k += 1u;
 
     int status = COSMICA_PATH_RUNNING;
     if (!x.finite()) status = COSMICA_PATH_NONFINITE;
-    else if ((EXT && q.sq != 0.0f) ? m32::outside_squashed(q, x.fr(), x.fth(), x.fph()) : x.exited())
+    else if ((EXT && P32F(q, sq) != 0.0f) ? m32::outside_squashed(q, x.fr(), x.fth(), x.fph()) : x.exited())
         status = COSMICA_PATH_EXIT;
     else if (L.k >= L.max_steps) status = COSMICA_PATH_STEP_LIMIT;
     if (status == COSMICA_PATH_RUNNING) return false;
@@ -217,7 +217,7 @@ __global__ void k_debug_eval32(const DevParams *__restrict__ prm, const DevSpeci
     if (i >= n) return;
     float dbg[kDebugEvalN];
     m32::Drift c;
-    m32::eval<true>(prm[0].f, spc[0].aoz_m0_sq, spc[0].sgnq, (float)st[4 * i], (float)st[4 * i + 1],
+    m32::eval<true>(P32{reinterpret_cast<const float *>(&prm[0].f), 1u}, spc[0].aoz_m0_sq, spc[0].sgnq, (float)st[4 * i], (float)st[4 * i + 1],
               (float)st[4 * i + 2], (float)st[4 * i + 3], c, dbg);
     for (int j = 0; j < kDebugEvalN; ++j) out[(size_t)i * kDebugEvalN + j] = dbg[j];
 }

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 
@@ -133,7 +134,8 @@ extern "C" cosmica_status cosmica_propagate_noalloc(const cosmica_params *params
 
     LaunchArgs a{d_prm, d_spc, d_items, d_prefix, n_energies, total,
                  ExitPtrs{out->r, out->th, out->ph, out->lnP, out->s, out->steps, out->status, out->item, out->lw},
-                 d_counters + 1, d_counters, nullptr, d_prefix};
+                 d_counters + 1, d_counters, nullptr, d_prefix,
+                 reinterpret_cast<const float *>(base + kOffParams + offsetof(DevParams, f)), 1u};   // in place
     if (params->precision == COSMICA_PREC_FP64) {
         e = launch_propagate_fp64(a, s);
     } else {

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
                     const DevParams &p = a.prm[rec.slot];
                     const DevSpecies &sp = a.spc[rec.slot];
                     load<ACC>(x, rec, p);
-                    S.L.q = &p.f;
+                    S.L.q = reinterpret_cast<const float *>(&p.f);
                     S.L.M2 = sp.aoz_m0_sq;
                     S.L.sq = sp.sgnq;
                     S.L.pid = rec.pid;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
                         const DevParams &p = a.prm[item.slot];
                         const DevSpecies &sp = a.spc[item.slot];
                         const uint64_t off = g - a.prefix[it];
-                        S.L.q = &p.f;
+                        S.L.q = reinterpret_cast<const float *>(&p.f);
                         S.L.M2 = sp.aoz_m0_sq;
                         S.L.sq = sp.sgnq;
                         S.L.pid = item.first_pid + off;
@@ -142,14 +142,14 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
         float z0, z1, z2;
         m32::normals(S.L.seed, S.L.pid, S.L.k, z0, z1, z2);
         m32::Drift c;
-        const F32Params &q = *S.L.q;
+        const P32 q{S.L.q, 1u};
         m32::eval<false>(q, S.L.M2, S.L.sq, x.fr(), x.fth(), x.fph(), x.flnP(), c);
         const float sdt = sqrtf(c.dt);
         const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
         const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);
         const float dph = fmaf(c.dph_drift, c.dt, fmaf(c.l20, z0, c.l22 * z2) * sdt * c.inv_rs);
         x.add(dr, dth, dph, c.dlnP * c.dt, c.dt);
-        x.boundaries(q.r_in);
+        x.boundaries(P32F(q, r_in));
         S.L.k += 1u;
         used += 1u;
 

@@ -9,7 +9,7 @@
 namespace cosmica {
 
 struct Lane {
-    const F32Params *q;
+    const float *q;            // field 0 of the particle's FP32 parameter block (see P32)
     float M2, sq;
     uint64_t pid, seed, g;
     uint32_t item, k, max_steps;

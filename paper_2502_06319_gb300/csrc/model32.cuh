@@ -52,27 +52,27 @@ struct Drift {
 // Radial shells (Sec. II.B): the shells a, b whose values blend at r and the
 // smoothstep weight S(x) = x^2 (3 - 2x) with its radial derivative; a = b and
 // S = 0 away from the edge windows, so v[a] + (v[b] - v[a]) S is the shell's value.
-__device__ __forceinline__ void shell_weights(const F32Params &q, float r, int &a, int &b, float &S, float &dS)
+__device__ __forceinline__ void shell_weights(const P32 &q, float r, int &a, int &b, float &S, float &dS)
 {
-    const int n = (int)q.n_sh;
-    const int k = min(max((int)(r * q.sh_inv_dr), 0), n - 1);
+    const int n = (int)P32F(q, n_sh);
+    const int k = min(max((int)(r * P32F(q, sh_inv_dr)), 0), n - 1);
     float x = 0.0f;
     a = k;
     b = k;
-    const float lo_edge = (float)k * q.sh_dr;
-    const float hi_edge = (float)(k + 1) * q.sh_dr;
-    if (k >= 1 && r < lo_edge + q.sh_w) {
+    const float lo_edge = (float)k * P32F(q, sh_dr);
+    const float hi_edge = (float)(k + 1) * P32F(q, sh_dr);
+    if (k >= 1 && r < lo_edge + P32F(q, sh_w)) {
         a = k - 1;
-        x = (r - (lo_edge - q.sh_w)) * q.sh_inv_2w;
-    } else if (k + 1 <= n - 1 && r > hi_edge - q.sh_w) {
+        x = (r - (lo_edge - P32F(q, sh_w))) * P32F(q, sh_inv_2w);
+    } else if (k + 1 <= n - 1 && r > hi_edge - P32F(q, sh_w)) {
         b = k + 1;
-        x = (r - (hi_edge - q.sh_w)) * q.sh_inv_2w;
+        x = (r - (hi_edge - P32F(q, sh_w))) * P32F(q, sh_inv_2w);
     }
     S = x * x * fmaf(-2.0f, x, 3.0f);
-    dS = 6.0f * x * (1.0f - x) * q.sh_inv_2w;
+    dS = 6.0f * x * (1.0f - x) * P32F(q, sh_inv_2w);
 }
 
-// Coefficients at (r, th, ph, lnP).  q: FP32 constants of the heliosphere.
+// Coefficients at (r, th, ph, lnP).  q: FP32 constants of the heliosphere (read through P32).
 // M2 = (A/|Z| m0)^2, sq = sign of the charge.
 // Nose-squashed spheroid (Sec. II.B) in FP32: distance R from the Sun along
 // the direction mu and dR/dmu; ia2 = 1/a^2, ib2 = 1/b^2, c = centre offset,
@@ -88,34 +88,34 @@ __device__ __forceinline__ float spheroid_radius(float ia2, float ib2, float c, 
 }
 
 // cos of the angle between the direction (th, ph) and the nose, with its derivatives
-__device__ __forceinline__ float nose_mu(const F32Params &q, float sn, float cs, float ph, float &dmu_dth,
+__device__ __forceinline__ float nose_mu(const P32 &q, float sn, float cs, float ph, float &dmu_dth,
                                          float &dmu_dph)
 {
-    float d = ph - q.nose_ph;                      // nose_ph in [0, 2 pi): d in (-2 pi, 2 pi)
+    float d = ph - P32F(q, nose_ph);                      // nose_ph in [0, 2 pi): d in (-2 pi, 2 pi)
     d = (d > kPiF) ? d - kTwoPiF : ((d < -kPiF) ? d + kTwoPiF : d);
     float sd, cd;
     __sincosf(d, &sd, &cd);
-    dmu_dth = fmaf(cs * q.sin_nth, cd, -sn * q.cos_nth);
-    dmu_dph = -sn * q.sin_nth * sd;
-    return fmaf(sn * q.sin_nth, cd, cs * q.cos_nth);
+    dmu_dth = fmaf(cs * P32F(q, sin_nth), cd, -sn * P32F(q, cos_nth));
+    dmu_dph = -sn * P32F(q, sin_nth) * sd;
+    return fmaf(sn * P32F(q, sin_nth), cd, cs * P32F(q, cos_nth));
 }
 
 // Outside the squashed outer spheroid (FP32; the spherical boundary keeps its exact test).
-__device__ __forceinline__ bool outside_squashed(const F32Params &q, float r, float th, float ph)
+__device__ __forceinline__ bool outside_squashed(const P32 &q, float r, float th, float ph)
 {
     float sn, cs, dth, dph;
     __sincosf(th, &sn, &cs);
     const float mu = nose_mu(q, sn, cs, ph, dth, dph);
-    const float xa = fmaf(r, mu, q.hp_c);
+    const float xa = fmaf(r, mu, P32F(q, hp_c));
     const float rp2 = r * r * fmaf(-mu, mu, 1.0f);
-    return fmaf(xa * xa, q.hp_ia2, rp2 * q.hp_ib2) >= 1.0f;
+    return fmaf(xa * xa, P32F(q, hp_ia2), rp2 * P32F(q, hp_ib2)) >= 1.0f;
 }
 
 // EXT: the parameter sets of the launch may have radial shells or a squashed
 // heliosphere (compile-time, so that launches of the basic model carry none of
 // that code or its registers).
 template <bool EXT>
-__device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, float r, float th, float ph,
+__device__ __forceinline__ void eval(const P32 &q, float M2, float sq, float r, float th, float ph,
                                      float lnP, Drift &o, float *dbg = nullptr)
 {
     const float P = __expf(lnP);
@@ -129,14 +129,14 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
 
     // wind V(th) and dV/dth
     const float lat = kHalfPiF - th;
-    const float sw = half_one_plus_tanh((fabsf(lat) - q.lat_f) * q.inv_dlat);
-    const float V = fmaf(q.dV, sw, q.Vs);
+    const float sw = half_one_plus_tanh((fabsf(lat) - P32F(q, lat_f)) * P32F(q, inv_dlat));
+    const float V = fmaf(P32F(q, dV), sw, P32F(q, Vs));
     const float sgn_lat = (lat > 0.0f) ? -1.0f : ((lat < 0.0f) ? 1.0f : 0.0f);   // d|lat|/dth
-    const float dV = q.dV * 2.0f * sw * (1.0f - sw) * q.inv_dlat * sgn_lat;
+    const float dV = P32F(q, dV) * 2.0f * sw * (1.0f - sw) * P32F(q, inv_dlat) * sgn_lat;
     const float inv_V = __fdividef(1.0f, V);
 
     // Parker spiral
-    const float Gam = q.Omega * r * sn * inv_V;
+    const float Gam = P32F(q, Omega) * r * sn * inv_V;
     const float G2 = Gam * Gam;
     const float iq = __fdividef(1.0f, fmaf(Gam, Gam, 1.0f));
     const float dGam_dth = Gam * fmaf(-dV, inv_V, cot);
@@ -144,17 +144,17 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
     // termination shock factor (uniform branch: no shock in the parameter set); a
     // squashed shock sits at its spheroid's distance along the point's direction
     float g = 1.0f, dg = 0.0f, dg_dth = 0.0f, dg_dph = 0.0f;
-    const bool squashed = EXT && q.sq != 0.0f;
-    if (q.ts_drop != 0.0f) {
-        float Rts = q.R_ts, dR_dmu = 0.0f, dmu_dth = 0.0f, dmu_dph = 0.0f;
+    const bool squashed = EXT && P32F(q, sq) != 0.0f;
+    if (P32F(q, ts_drop) != 0.0f) {
+        float Rts = P32F(q, R_ts), dR_dmu = 0.0f, dmu_dth = 0.0f, dmu_dph = 0.0f;
         if (squashed) {
             const float mu = nose_mu(q, sn, cs, ph, dmu_dth, dmu_dph);
-            Rts = q.ts_R * spheroid_radius(q.ts_ia2, q.ts_ib2, q.ts_c, q.ts_C, mu, dR_dmu);
-            dR_dmu *= q.ts_R;
+            Rts = P32F(q, ts_R) * spheroid_radius(P32F(q, ts_ia2), P32F(q, ts_ib2), P32F(q, ts_c), P32F(q, ts_C), mu, dR_dmu);
+            dR_dmu *= P32F(q, ts_R);
         }
-        const float st = half_one_plus_tanh((r - Rts) * q.inv_dts);
-        g = fmaf(-q.ts_drop, st, 1.0f);
-        const float w = q.ts_drop * 2.0f * st * (1.0f - st) * q.inv_dts;
+        const float st = half_one_plus_tanh((r - Rts) * P32F(q, inv_dts));
+        g = fmaf(-P32F(q, ts_drop), st, 1.0f);
+        const float w = P32F(q, ts_drop) * 2.0f * st * (1.0f - st) * P32F(q, inv_dts);
         dg = -w;
         if (squashed) {
             dg_dth = w * dR_dmu * dmu_dth;
@@ -164,16 +164,16 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
 
     // radial shells: K0 and the sheet tilt of the shell holding r (the single-region
     // tilt is read where the sheet needs it, so that it is not live before)
-    const bool shells = EXT && q.n_sh != 0.0f;
-    float K0 = q.K0, dK0 = 0.0f, sh_ta = 0.0f, sh_ta2 = 0.0f, dta = 0.0f;
+    const bool shells = EXT && P32F(q, n_sh) != 0.0f;
+    float K0 = P32F(q, K0), dK0 = 0.0f, sh_ta = 0.0f, sh_ta2 = 0.0f, dta = 0.0f;
     if (shells) {
         int a, b;
         float S, dS;
         shell_weights(q, r, a, b, S, dS);
-        const float Ka = q.sh_K0[a], dKab = q.sh_K0[b] - Ka;
+        const float Ka = P32A(q, sh_K0, a), dKab = P32A(q, sh_K0, b) - Ka;
         K0 = fmaf(dKab, S, Ka);
         dK0 = dKab * dS;
-        const float al = q.sh_alpha[a], dal = q.sh_alpha[b] - al;
+        const float al = P32A(q, sh_alpha, a), dal = P32A(q, sh_alpha, b) - al;
         float sa, ca;
         __sincosf(fmaf(dal, S, al), &sa, &ca);
         sh_ta = __fdividef(sa, ca);
@@ -186,15 +186,15 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
     const float Kpar = Kb * g;
     float dKpar = Kb * dg;
     if (shells) dKpar = fmaf(dK0 * beta * P, g, dKpar);
-    const float c2s = fmaf(q.er, G2 * iq, iq);            // cos^2 + er sin^2
+    const float c2s = fmaf(P32F(q, er), G2 * iq, iq);            // cos^2 + er sin^2
     const float iq2 = iq * iq;
     const float dc2_dr = -2.0f * G2 * iq2 * inv_r;         // d cos^2 psi / dr
     const float sc = Gam * iq;
     const float dsc_dr = Gam * (1.0f - G2) * iq2 * inv_r;
     const float Krr = Kpar * c2s;
-    const float erm1 = q.er - 1.0f;
+    const float erm1 = P32F(q, er) - 1.0f;
     const float Krp = erm1 * Kpar * sc;
-    const float Ktt = q.et * Kpar;
+    const float Ktt = P32F(q, et) * Kpar;
     const float dKrr = fmaf(dKpar, c2s, -Kpar * erm1 * dc2_dr);
     const float dKrp = erm1 * fmaf(dKpar, sc, Kpar * dsc_dr);
 
@@ -207,21 +207,21 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
         // K depends on th and ph through the squashed shock: d_th K_thth / r^2,
         // d_ph K_rph / (r sin th) and d_ph K_phph / (r sin th)^2
         const float dKpar_th = Kb * dg_dth, dKpar_ph = Kb * dg_dph;
-        Ath = fmaf(q.et * dKpar_th, inv_r * inv_r, Ath);
+        Ath = fmaf(P32F(q, et) * dKpar_th, inv_r * inv_r, Ath);
         Ar = fmaf(erm1 * dKpar_ph * sc, inv_rs, Ar);
-        Aph = fmaf(dKpar_ph * fmaf(q.er, iq, G2 * iq), inv_rs * inv_rs, Aph);
+        Aph = fmaf(dKpar_ph * fmaf(P32F(q, er), iq, G2 * iq), inv_rs * inv_rs, Aph);
     }
 
     // Cholesky factor of 2K
     const float rK = rsqrtf(Krr);
     o.l00 = kSqrt2F * Krr * rK;
     o.l20 = kSqrt2F * Krp * rK;
-    o.l22 = q.sqrt2er * Kpar * rK;
+    o.l22 = P32F(q, sqrt2er) * Kpar * rK;
     o.l11 = sqrtf(2.0f * Ktt);
 
     // drift v_d = sgn(qA) curl(kappa_A h e_B)
     float vd0 = 0.0f, vd1 = 0.0f, vd2 = 0.0f, delta = 0.0f, h = 1.0f;
-    if (q.drift != 0.0f) {
+    if (P32F(q, drift) != 0.0f) {
         const float r2 = r * r;
         const float F = r2 * iq;
         const float Gf = F * Gam;
@@ -229,30 +229,30 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
         const float dGf_dr = r * Gam * (3.0f + G2) * iq2;
         const float dGf_dth = r2 * dGam_dth * (1.0f - G2) * iq2;
         float hr = 0.0f, ht = 0.0f, hp = 0.0f;
-        if (q.hcs != 0.0f) {
-            const float phs = fmaf(q.Omega * r, inv_V, ph);
-            const float dphs_dr = q.Omega * inv_V;
-            const float dphs_dth = -q.Omega * r * dV * inv_V * inv_V;
+        if (P32F(q, hcs) != 0.0f) {
+            const float phs = fmaf(P32F(q, Omega) * r, inv_V, ph);
+            const float dphs_dr = P32F(q, Omega) * inv_V;
+            const float dphs_dth = -P32F(q, Omega) * r * dV * inv_V * inv_V;
             // nearest integer by the 1.5 2^23 shift (|phs| / 2 pi < 2^22): two FADDs
             const float turns = __fsub_rn(__fadd_rn(phs * kInvTwoPiF, 12582912.0f), 12582912.0f);
             const float red = fmaf(-kTwoPiF, turns, phs);
             float sp, cp;
             __sincosf(red, &sp, &cp);
-            const float ta = shells ? sh_ta : q.ta;
-            const float ta2 = shells ? sh_ta2 : q.ta2;
+            const float ta = shells ? sh_ta : P32F(q, ta);
+            const float ta2 = shells ? sh_ta2 : P32F(q, ta2);
             const float th_cs = kHalfPiF + atanf(ta * sp);
             const float inv_den = __fdividef(1.0f, fmaf(ta2, sp * sp, 1.0f));
             const float dthcs = (ta * cp) * inv_den;
             const float sqiq = sqrtf(iq);
-            const float w_rl = q.D2 * P * r * sqiq;
+            const float w_rl = P32F(q, D2) * P * r * sqiq;
             float dd_dr = 0.0f, dd_dth = 0.0f;
-            if (w_rl > q.dcs_min) {
+            if (w_rl > P32F(q, dcs_min)) {
                 delta = w_rl;
-                const float k3 = q.D2 * P * iq * sqiq;
+                const float k3 = P32F(q, D2) * P * iq * sqiq;
                 dd_dr = k3;
                 dd_dth = -k3 * r * Gam * dGam_dth;
             } else {
-                delta = q.dcs_min;
+                delta = P32F(q, dcs_min);
             }
             const float inv_d = __fdividef(1.0f, delta);
             const float u = (th_cs - th) * inv_d;
@@ -265,7 +265,7 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
             ht = sech2 * fmaf(-u, dd_dth, fmaf(dthcs, dphs_dth, -1.0f)) * inv_d;
             hp = sech2 * dthcs * inv_d;
         }
-        const float s = sq * q.polarity * q.CA0 * beta * P * inv_r;
+        const float s = sq * P32F(q, polarity) * P32F(q, CA0) * beta * P * inv_r;
         const float Wph = -h * Gf;                       // W_ph / C_A
         const float dWph_dth = -fmaf(ht, Gf, h * dGf_dth);
         const float dWph_dr = -fmaf(hr, Gf, h * dGf_dr);
@@ -284,21 +284,21 @@ __device__ __forceinline__ void eval(const F32Params &q, float M2, float sq, flo
 
     // step length
     float dt;
-    if (q.dt_fixed > 0.0f) {
-        dt = q.dt_fixed;
+    if (P32F(q, dt_fixed) > 0.0f) {
+        dt = P32F(q, dt_fixed);
     } else {
-        const float t1 = __fdividef(q.eps_adv2 * Krr, Ar_tot * Ar_tot);
-        const float t2 = __fdividef(q.eps_diff * r * r, Krr);
-        dt = fminf(q.dt_max, fminf(t1, t2));
+        const float t1 = __fdividef(P32F(q, eps_adv2) * Krr, Ar_tot * Ar_tot);
+        const float t2 = __fdividef(P32F(q, eps_diff) * r * r, Krr);
+        dt = fminf(P32F(q, dt_max), fminf(t1, t2));
         if (delta > 0.0f) {
             const float rd = r * delta;
-            dt = fminf(dt, __fdividef(q.eps_diff * rd * rd, Ktt));
+            dt = fminf(dt, __fdividef(P32F(q, eps_diff) * rd * rd, Ktt));
         }
-        dt = fmaxf(dt, q.dt_min);
+        dt = fmaxf(dt, P32F(q, dt_min));
     }
     o.dt = dt;
     if (dbg) {
-        dbg[0] = V; dbg[1] = Gam; dbg[2] = Kpar; dbg[3] = Krr; dbg[4] = Ktt; dbg[5] = Kpar * fmaf(G2, iq, q.er * iq);
+        dbg[0] = V; dbg[1] = Gam; dbg[2] = Kpar; dbg[3] = Krr; dbg[4] = Ktt; dbg[5] = Kpar * fmaf(G2, iq, P32F(q, er) * iq);
         dbg[6] = Krp; dbg[7] = Ar; dbg[8] = Ath; dbg[9] = Aph; dbg[10] = o.l00; dbg[11] = o.l11;
         dbg[12] = o.l20; dbg[13] = o.l22; dbg[14] = h; dbg[15] = delta;
         dbg[16] = vd0; dbg[17] = vd1; dbg[18] = vd2; dbg[19] = o.dlnP; dbg[20] = dt;

@@ -66,9 +66,11 @@ def test_graph_replay_and_batch_spectrum():
     arr = cz.make_items(items)
     total = sum(i[3] for i in items)
     s = t.cuda.Stream()
-    res = []
+    res, outs = [], []
     for rep in range(3):
+        # all three buffers stay alive, so every replay writes to new addresses
         out = cz.ExitBuffers(total)
+        outs.append(out)
         steps = t.zeros(1, dtype=t.int64, device="cuda")
         tune = cz.cosmica_tuning(128, 0, 64, 1, 1)
         with t.cuda.stream(s):
