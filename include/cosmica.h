@@ -276,7 +276,7 @@ cosmica_status cosmica_propagate_orbit(cosmica_model *model, const cosmica_speci
  * Same arguments and results as cosmica_propagate, with the parameter set
  * passed directly instead of a model handle.  The library's scratch for the
  * call (parameter block, species, work items, prefix sums, queue cursor,
- * step counter) is a fixed static device array of about 75 KB that every GPU
+ * step counter) is a fixed static device array of about 95 KB that every GPU
  * loading the library holds until the process exits; the call makes no
  * cudaMalloc, cudaFree or other allocating call.
  *   n_energies   at most COSMICA_NOALLOC_MAX_ENERGIES (INVALID otherwise)

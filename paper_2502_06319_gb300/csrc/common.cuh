@@ -73,18 +73,31 @@ struct DevParams {
 };
 
 // Read-only view of one parameter set's FP32 block in a table whose consecutive
-// fields lie `stride` floats apart: stride 1 reads one F32Params in place; a
-// batch of n sets uses a field-major table (field f of set i at f * n + i), so
-// that the lanes of a warp reading one field of different sets touch adjacent
-// words of one or two cache lines instead of one line per set.
+// fields lie S floats apart (a compile-time stride, so every field is an
+// immediate offset from one per-lane pointer).  S = 1 reads one F32Params in
+// place.  The mixed kernels read the paged field-major table (S = kSetsPerPage):
+// page k holds sets 64k .. 64k+63, field f of set i at
+// k * kF32Fields * 64 + f * 64 + i % 64, so the lanes of a warp reading one
+// field of different sets touch adjacent words of at most two cache lines
+// instead of one line per set (and different L1 banks).
+template <uint32_t S>
 struct P32 {
     const float *__restrict__ p;   // field 0 of the set
-    uint32_t stride;
-    __device__ __forceinline__ float at(uint32_t field) const { return __ldg(p + field * stride); }
+    __device__ __forceinline__ float at(uint32_t field) const { return __ldg(p + field * S); }
 };
+constexpr uint32_t kSetsPerPage = 64;
 #define P32F(q, m) ((q).at((uint32_t)(offsetof(F32Params, m) / sizeof(float))))
 #define P32A(q, m, k) ((q).at((uint32_t)(offsetof(F32Params, m) / sizeof(float)) + (uint32_t)(k)))
 constexpr uint32_t kF32Fields = sizeof(F32Params) / sizeof(float);
+// floats of the paged field-major table for n sets, and the offset of set i's field 0
+__host__ __device__ constexpr size_t f32_table_floats(uint32_t n)
+{
+    return (size_t)((n + kSetsPerPage - 1) / kSetsPerPage) * kF32Fields * kSetsPerPage;
+}
+__host__ __device__ constexpr size_t f32_table_offset(uint32_t i)
+{
+    return (size_t)(i / kSetsPerPage) * kF32Fields * kSetsPerPage + i % kSetsPerPage;
+}
 static_assert(sizeof(F32Params) % sizeof(float) == 0, "F32Params holds floats only");
 
 struct DevSpecies {

@@ -368,7 +368,7 @@ using namespace cosmica::host;
 struct cosmica_model {
     cosmica_params p;
     DevParams *d_prm = nullptr;
-    const float *d_f32 = nullptr;   // field-major FP32 block (inside the d_prm allocation)
+    const float *d_f32 = nullptr;   // paged field-major FP32 block (inside the d_prm allocation)
     DevBuf spc;                 // DevSpecies[1] + spectrum items
     Staging spc_stage;
     Tables tab;
@@ -426,15 +426,15 @@ extern "C" void cosmica_params_default(cosmica_params *p)
 }
 
 // Upload n parameter sets, derive their constants on the device, and lay out
-// their FP32 blocks field-major right after them in the same allocation
-// (*f32: field f of set i at f * n + i), the layout the mixed kernels read.
+// their FP32 blocks paged field-major right after them in the same allocation
+// (*f32, see P32), the layout the mixed kernels read.
 static cosmica_status upload_params(const cosmica_params *ps, uint32_t n, DevParams **out, const float **f32)
 {
     std::vector<DevParams> h(n);
     for (uint32_t i = 0; i < n; ++i) h[i] = to_dev(ps[i]);
     const size_t b_prm = align_up(n * sizeof(DevParams), 256);
     char *d = nullptr;
-    CK(cudaMalloc(&d, b_prm + (size_t)n * kF32Fields * sizeof(float)), "cudaMalloc(params)");
+    CK(cudaMalloc(&d, b_prm + f32_table_floats(n) * sizeof(float)), "cudaMalloc(params)");
     DevParams *dp = reinterpret_cast<DevParams *>(d);
     float *table = reinterpret_cast<float *>(d + b_prm);
     cudaError_t e = cudaMemcpy(dp, h.data(), n * sizeof(DevParams), cudaMemcpyHostToDevice);
@@ -526,7 +526,7 @@ static cosmica_status propagate_items(cosmica_model *m, const cosmica_species *s
     }
     CK(cudaMemsetAsync(m->tab.counters, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
     LaunchArgs a{m->d_prm, d_sp, m->tab.items, m->tab.prefix, m->tab.n_items, total, ex,
-                 m->tab.counters + 1, m->tab.counters, m->tab.qitem, m->tab.qprefix, m->d_f32, 1u};
+                 m->tab.counters + 1, m->tab.counters, m->tab.qitem, m->tab.qprefix, m->d_f32};
     cudaError_t e;
     if (m->p.precision == COSMICA_PREC_FP64) {
         e = launch_propagate_fp64(a, s);
@@ -763,7 +763,7 @@ struct cosmica_batch {
     int precision = 0;
     bool extended = false;     // some parameter set has radial shells or a squashed heliosphere
     DevParams *d_prm = nullptr;
-    const float *d_f32 = nullptr;   // field-major FP32 blocks (inside the d_prm allocation)
+    const float *d_f32 = nullptr;   // paged field-major FP32 blocks (inside the d_prm allocation)
     DevSpecies *d_spc = nullptr;
     Tables tab;
     MixedVariant variant() const { return MixedVariant{precision, params[0].formulation == 1, extended}; }
@@ -878,8 +878,7 @@ static cosmica_status batch_launch(cosmica_batch *b, uint64_t total, const ExitP
                                    const cosmica_tuning *tuning, cudaStream_t s)
 {
     LaunchArgs a{b->d_prm, b->d_spc, b->tab.items, b->tab.prefix, b->tab.n_items, total, ex,
-                 b->tab.counters + 1, b->tab.counters, b->tab.qitem, b->tab.qprefix, b->d_f32,
-                 (uint32_t)b->params.size()};
+                 b->tab.counters + 1, b->tab.counters, b->tab.qitem, b->tab.qprefix, b->d_f32};
     auto direct = [&]() -> cosmica_status {
         CK(cudaMemsetAsync(b->tab.counters, 0, 2 * sizeof(unsigned long long), s), "cudaMemsetAsync(counters)");
         cudaError_t e = (b->precision == COSMICA_PREC_FP64)
@@ -1064,8 +1063,12 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
         for (unsigned blk : blocks) {
             for (unsigned per : periods) {
                 const unsigned maxb = (unsigned)std::max(1, mixed_max_blocks_per_sm(b->variant(), blk, per != 0));
+                // all resident blocks, one fewer, and half: fewer resident warps can win when the
+                // register file or the L1 is the contended resource
                 cands.push_back(cosmica_tuning{blk, maxb, per, 0, 1});
-                if (maxb / 2 >= 1 && maxb / 2 != maxb) cands.push_back(cosmica_tuning{blk, maxb / 2, per, 0, 1});
+                if (maxb >= 3) cands.push_back(cosmica_tuning{blk, maxb - 1, per, 0, 1});
+                if (maxb / 2 >= 1 && maxb / 2 != maxb && maxb / 2 != maxb - 1)
+                    cands.push_back(cosmica_tuning{blk, maxb / 2, per, 0, 1});
             }
         }
         for (const cosmica_tuning &t : cands) {

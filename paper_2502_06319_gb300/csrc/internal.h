@@ -23,8 +23,7 @@ struct LaunchArgs {
     unsigned long long *cursor;        // work-queue cursor (persistent kernels)
     const uint32_t *qitem;             // item of each queue slot (null: item order)
     const uint64_t *qprefix;           // prefix sums of particle counts in queue order
-    const float *f32;                  // FP32 blocks of the parameter sets, field-major (P32)
-    uint32_t f32_stride;               // = number of parameter sets in that table
+    const float *f32;                  // FP32 blocks of the parameter sets, paged field-major (P32)
 };
 
 struct PersistentShape {

@@ -33,7 +33,7 @@ __device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t q, 
     const DevItem item = a.items[it];
     const DevParams &p = a.prm[item.param_idx];
     const DevSpecies &sp = a.spc[item.species_idx];
-    L.q = a.f32 + item.param_idx;
+    L.q = a.f32 + f32_table_offset(item.param_idx);
     L.M2 = sp.aoz_m0_sq;
     L.sq = sp.sgnq;
     L.pid = item.first_pid + local;
@@ -57,7 +57,7 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
     float z0, z1, z2;
     m32::normals(L.seed, L.pid, L.k, z0, z1, z2);
     m32::Drift c;
-    const P32 q{L.q, a.f32_stride};
+    const P32<kSetsPerPage> q{L.q};
     float lnP;
     if constexpr (EN) {
         // rigidity from the integrated kinetic energy: P = (A/|Z|) sqrt(T (T + 2 m0))
@@ -66,7 +66,7 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
     } else {
         lnP = x.flnP();
     }
-    m32::eval<EXT>(q, L.M2, L.sq, x.fr(), x.fth(), x.fph(), lnP, c);
+    m32::eval<EXT, kSetsPerPage>(q, L.M2, L.sq, x.fr(), x.fth(), x.fph(), lnP, c);
     const float sdt = sqrtf(c.dt);
     const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
     const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);
@@ -217,7 +217,7 @@ __global__ void k_debug_eval32(const DevParams *__restrict__ prm, const DevSpeci
     if (i >= n) return;
     float dbg[kDebugEvalN];
     m32::Drift c;
-    m32::eval<true>(P32{reinterpret_cast<const float *>(&prm[0].f), 1u}, spc[0].aoz_m0_sq, spc[0].sgnq, (float)st[4 * i], (float)st[4 * i + 1],
+    m32::eval<true, 1>(P32<1>{reinterpret_cast<const float *>(&prm[0].f)}, spc[0].aoz_m0_sq, spc[0].sgnq, (float)st[4 * i], (float)st[4 * i + 1],
               (float)st[4 * i + 2], (float)st[4 * i + 3], c, dbg);
     for (int j = 0; j < kDebugEvalN; ++j) out[(size_t)i * kDebugEvalN + j] = dbg[j];
 }

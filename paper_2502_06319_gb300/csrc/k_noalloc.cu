@@ -49,7 +49,8 @@ constexpr size_t kOffSpecies = (sizeof(DevParams) + 255) / 256 * 256;
 constexpr size_t kOffItems = kOffSpecies + 256;
 constexpr size_t kOffPrefix = kOffItems + (kMaxE * sizeof(DevItem) + 255) / 256 * 256;
 constexpr size_t kOffCounters = kOffPrefix + ((kMaxE + 1) * sizeof(uint64_t) + 255) / 256 * 256;
-constexpr size_t kScratchBytes = kOffCounters + 256;
+constexpr size_t kOffF32 = kOffCounters + 256;          // one page of the FP32 parameter table
+constexpr size_t kScratchBytes = kOffF32 + (f32_table_floats(1) * sizeof(float) + 255) / 256 * 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -118,6 +119,7 @@ extern "C" cosmica_status cosmica_propagate_noalloc(const cosmica_params *params
     DevItem *d_items = (DevItem *)(base + kOffItems);
     uint64_t *d_prefix = (uint64_t *)(base + kOffPrefix);
     unsigned long long *d_counters = (unsigned long long *)(base + kOffCounters);
+    float *d_f32 = (float *)(base + kOffF32);
 
     cudaStream_t s = (cudaStream_t)stream;
     const DevParams hp = to_dev(*params);
@@ -130,12 +132,12 @@ extern "C" cosmica_status cosmica_propagate_noalloc(const cosmica_params *params
                                               cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counters, 0, 2 * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = launch_derive(d_prm, 1, s);
+    if (e == cudaSuccess) e = launch_f32_table(d_prm, 1, d_f32, s);
     if (e != cudaSuccess) return cuda_fail(e, "cosmica_propagate_noalloc set-up");
 
     LaunchArgs a{d_prm, d_spc, d_items, d_prefix, n_energies, total,
                  ExitPtrs{out->r, out->th, out->ph, out->lnP, out->s, out->steps, out->status, out->item, out->lw},
-                 d_counters + 1, d_counters, nullptr, d_prefix,
-                 reinterpret_cast<const float *>(base + kOffParams + offsetof(DevParams, f)), 1u};   // in place
+                 d_counters + 1, d_counters, nullptr, d_prefix, d_f32};
     if (params->precision == COSMICA_PREC_FP64) {
         e = launch_propagate_fp64(a, s);
     } else {

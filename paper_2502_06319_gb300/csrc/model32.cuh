@@ -52,7 +52,8 @@ struct Drift {
 // Radial shells (Sec. II.B): the shells a, b whose values blend at r and the
 // smoothstep weight S(x) = x^2 (3 - 2x) with its radial derivative; a = b and
 // S = 0 away from the edge windows, so v[a] + (v[b] - v[a]) S is the shell's value.
-__device__ __forceinline__ void shell_weights(const P32 &q, float r, int &a, int &b, float &S, float &dS)
+template <uint32_t ST>
+__device__ __forceinline__ void shell_weights(const P32<ST> &q, float r, int &a, int &b, float &S, float &dS)
 {
     const int n = (int)P32F(q, n_sh);
     const int k = min(max((int)(r * P32F(q, sh_inv_dr)), 0), n - 1);
@@ -88,7 +89,8 @@ __device__ __forceinline__ float spheroid_radius(float ia2, float ib2, float c, 
 }
 
 // cos of the angle between the direction (th, ph) and the nose, with its derivatives
-__device__ __forceinline__ float nose_mu(const P32 &q, float sn, float cs, float ph, float &dmu_dth,
+template <uint32_t ST>
+__device__ __forceinline__ float nose_mu(const P32<ST> &q, float sn, float cs, float ph, float &dmu_dth,
                                          float &dmu_dph)
 {
     float d = ph - P32F(q, nose_ph);                      // nose_ph in [0, 2 pi): d in (-2 pi, 2 pi)
@@ -101,7 +103,8 @@ __device__ __forceinline__ float nose_mu(const P32 &q, float sn, float cs, float
 }
 
 // Outside the squashed outer spheroid (FP32; the spherical boundary keeps its exact test).
-__device__ __forceinline__ bool outside_squashed(const P32 &q, float r, float th, float ph)
+template <uint32_t ST>
+__device__ __forceinline__ bool outside_squashed(const P32<ST> &q, float r, float th, float ph)
 {
     float sn, cs, dth, dph;
     __sincosf(th, &sn, &cs);
@@ -114,8 +117,8 @@ __device__ __forceinline__ bool outside_squashed(const P32 &q, float r, float th
 // EXT: the parameter sets of the launch may have radial shells or a squashed
 // heliosphere (compile-time, so that launches of the basic model carry none of
 // that code or its registers).
-template <bool EXT>
-__device__ __forceinline__ void eval(const P32 &q, float M2, float sq, float r, float th, float ph,
+template <bool EXT, uint32_t ST>
+__device__ __forceinline__ void eval(const P32<ST> &q, float M2, float sq, float r, float th, float ph,
                                      float lnP, Drift &o, float *dbg = nullptr)
 {
     const float P = __expf(lnP);
