@@ -51,6 +51,22 @@ ALG_INST_PER_STEP = {"fp32": 260, "sfu": 31, "int_rng": 66, "compare": 14}
 ALG_INST_TS = {"fp32": 9, "sfu": 2}
 SM_LANES_PER_CLK = 128      # 4 SMSPs x 32 lanes: one warp instruction per SMSP per clock
 
+# DRAM bytes (read + write) of one propagation launch of the default workload (config 2),
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; the command is in
+# profiles/launches_bench_c2.md).  They describe the kernel built from the sources whose
+# SHA-256 is recorded; any other build reports traffic null.
+TRAFFIC_C2 = {"bytes_per_launch": None, "sources_sha256": None}
+KERNEL_SOURCES = ("common.cuh", "philox.cuh", "model32.cuh", "mixed_state.cuh", "k_mixed.cu")
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2502_06319_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -318,8 +334,17 @@ def main():
 
     sp0 = cz.make_species(jobs[0].species)
 
-    def one_pass(b, t):
+    kernel_ms = []      # propagation launches alone, CUDA events on the launching stream
+
+    def one_pass(b, t, time_kernel=False):
+        if time_kernel:
+            k0 = torch.cuda.Event(enable_timing=True)
+            k1 = torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
         cz.cosmica_batch_run(b, arr, nI, out, tuning=t, steps_out=steps_dev, stream=stream)
+        if time_kernel:
+            k1.record(stream)
+            kernel_ms.append((k0, k1))
         if energy:   # loss-weighted Eq. 4 (items are the energies of one job, in exit order)
             cz.cosmica_spectrum_unbinned(out, sp0, jobs[0].T_in, jobs[0].n_per_energy, 1, J, S, stream=stream)
         else:
@@ -340,7 +365,7 @@ def main():
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                one_pass(b, t)
+                one_pass(b, t, time_kernel=True)
                 e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -355,6 +380,8 @@ def main():
     clocks.start()
     ms, steps_done, launches = timed(batch, tune, args.warmup, args.steps)
     clk = clocks.stop()
+    kern_ms = sum(k0.elapsed_time(k1) for k0, k1 in kernel_ms)
+    kern_launches = len(kernel_ms)
     tot_ms = sum(ms)
     tot_ms, steps_all = reduce_timing(dist, tot_ms, float(steps_done), device="cuda")
     steps_per_s = steps_all / (tot_ms * 1e-3)
@@ -381,7 +408,7 @@ def main():
         if it > 0:
             e2e_s += dt
             e2e_steps += int(steps_dev.item())
-    h2d = nI * 32 + (nI + 1) * 8
+    h2d = nI * 64 + 2 * (nI + 1) * 8 + nI * 4     # work items, two prefix-sum tables, queue order
     d2h = 2 * nI * 8 + nI * (nb + 3) * 8
 
     # plain FP64 GPU path on the same workload (one-thread-per-particle launch)
@@ -403,11 +430,20 @@ def main():
         for k, v in ALG_INST_TS.items():
             alg[k] += v
     alg_total = sum(alg.values())
-    achieved = alg_total * steps_per_s / world / 1e12
+    # achieved: algorithmic issue slots of one launch (tally x the launch's steps) / the launch's
+    # average duration (CUDA events around the propagation call alone, this rank)
+    achieved = alg_total * (steps_done / max(1, kern_launches)) / (kern_ms / max(1, kern_launches) * 1e-3) / 1e12
+    traffic = None
+    if (args.workload == "c2" and args.scale == 1.0 and not energy and prec == cz.PREC_MIXED
+            and TRAFFIC_C2["bytes_per_launch"] is not None
+            and TRAFFIC_C2["sources_sha256"] == kernel_sources_sha256()):
+        traffic = TRAFFIC_C2["bytes_per_launch"]
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
-            "traffic": None, "peak_basis": f"{SM_LANES_PER_CLK} lanes/clk/SM x {sm_count} SMs x "
-                                           f"{f_mhz:.0f} MHz (median SM clock sampled under load)",
-            "alg_inst_per_step": alg, "alg_inst_total": alg_total}
+            "traffic": traffic, "peak_basis": f"{SM_LANES_PER_CLK} lanes/clk/SM x {sm_count} SMs x "
+                                              f"{f_mhz:.0f} MHz (median SM clock sampled under load)",
+            "alg_inst_per_step": alg, "alg_inst_total": alg_total,
+            "kernel_ms_per_launch": kern_ms / max(1, kern_launches),
+            "algorithmic_bytes_per_step": 0.0}
 
     line = {"metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,

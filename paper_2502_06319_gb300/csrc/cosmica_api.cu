@@ -531,7 +531,8 @@ static cosmica_status propagate_items(cosmica_model *m, const cosmica_species *s
     if (m->p.precision == COSMICA_PREC_FP64) {
         e = launch_propagate_fp64(a, s);
     } else {
-        const MixedVariant v{m->p.precision, m->p.formulation == 1, m->p.n_shells > 0 || m->p.squashed != 0};
+        const MixedVariant v{m->p.precision, m->p.formulation == 1, m->p.n_shells > 0 || m->p.squashed != 0,
+                             full_model(m->p)};
         e = launch_propagate_mixed(a, v, shape_for(v, nullptr, total), s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "propagation kernel launch");
@@ -762,11 +763,12 @@ struct cosmica_batch {
     std::vector<cosmica_species> species;
     int precision = 0;
     bool extended = false;     // some parameter set has radial shells or a squashed heliosphere
+    bool full = true;          // every parameter set is the full model (see full_model)
     DevParams *d_prm = nullptr;
     const float *d_f32 = nullptr;   // paged field-major FP32 blocks (inside the d_prm allocation)
     DevSpecies *d_spc = nullptr;
     Tables tab;
-    MixedVariant variant() const { return MixedVariant{precision, params[0].formulation == 1, extended}; }
+    MixedVariant variant() const { return MixedVariant{precision, params[0].formulation == 1, extended, full}; }
     ExitStage exit_stage;
     DevBuf spec_items, lis_buf;
     Staging spec_stage, lis_stage;
@@ -818,8 +820,10 @@ extern "C" cosmica_status cosmica_batch_create(const cosmica_params *params, uin
     b->params.assign(params, params + n_params);
     b->species.assign(species, species + n_species);
     b->precision = params[0].precision;
-    for (uint32_t i = 0; i < n_params; ++i)
+    for (uint32_t i = 0; i < n_params; ++i) {
         b->extended = b->extended || params[i].n_shells > 0 || params[i].squashed != 0;
+        b->full = b->full && full_model(params[i]);
+    }
     cosmica_status st = upload_params(params, n_params, &b->d_prm, &b->d_f32);
     if (st == COSMICA_OK) {
         std::vector<DevSpecies> hs(n_species);
@@ -1008,7 +1012,7 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
     int size_class = 0;
     while ((n_all >> size_class) > 1) ++size_class;
     // the kernel variant (energy form, shells) has its own registers, hence its own best shape
-    const int variant = (b->params[0].formulation == 1 ? 1 : 0) | (b->extended ? 2 : 0);
+    const int variant = (b->params[0].formulation == 1 ? 1 : 0) | (b->extended ? 2 : 0) | (b->full ? 4 : 0);
     const auto key = std::make_tuple(dev, b->precision, drift, ts, size_class, variant);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);

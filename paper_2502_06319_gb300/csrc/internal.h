@@ -86,7 +86,13 @@ struct MixedVariant {
     int acc;        // COSMICA_PREC_MIXED or COSMICA_PREC_MIXED_F64ACC
     bool energy;    // energy formulation (Eq. 1) instead of the momentum form
     bool extended;  // some parameter set of the launch has radial shells or a squashed heliosphere
+    bool full;      // every set is the full model: drift and current sheet on, adaptive step
 };
+// a set is the full model of the mixed kernels' FULL variant
+inline bool full_model(const cosmica_params &p)
+{
+    return !p.isotropic && p.drift_on && p.hcs_on && !(p.dt_fixed_day > 0.0);
+}
 cudaError_t launch_propagate_mixed(const LaunchArgs &a, MixedVariant v, PersistentShape shape, cudaStream_t s);
 int mixed_max_blocks_per_sm(MixedVariant v, unsigned block, bool compact);
 

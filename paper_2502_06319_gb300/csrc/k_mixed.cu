@@ -50,7 +50,7 @@ __device__ __forceinline__ void start_particle(const LaunchArgs &a, uint64_t q, 
 
 // One Euler-Maruyama step (Eq. 3, Eq. 6) of an active lane; true when the path ended
 // (exit record written).
-template <int ACC, bool EN, bool EXT>
+template <int ACC, bool EN, bool EXT, bool FULL>
 __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, EnergyAcc<ACC, EN> &en,
                                      unsigned long long &my_steps)
 {
@@ -66,7 +66,7 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
     } else {
         lnP = x.flnP();
     }
-    m32::eval<EXT, kSetsPerPage>(q, L.M2, L.sq, x.fr(), x.fth(), x.fph(), lnP, c);
+    m32::eval<EXT, FULL, kSetsPerPage>(q, L.M2, L.sq, x.fr(), x.fth(), x.fph(), lnP, c);
     const float sdt = sqrtf(c.dt);
     const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
     const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);
@@ -112,7 +112,7 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
 // they need, repacked through shared memory into the block's lowest lanes, so that
 // issued warp instructions keep carrying full lanes while the long tail of exit
 // times plays out.  Both phases share one step site (one copy of the step code).
-template <int ACC, bool COMPACT, bool EN, bool EXT>
+template <int ACC, bool COMPACT, bool EN, bool EXT, bool FULL>
 __global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a, uint32_t period)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a, uint32_t 
             // an idle warp goes straight to the next checkpoint
             tick = __any_sync(0xffffffffu, active) ? (tick + 1 == period ? 0 : tick + 1) : 0;
         }
-        if (active && step<ACC, EN, EXT>(a, L, x, en, my_steps)) active = false;
+        if (active && step<ACC, EN, EXT, FULL>(a, L, x, en, my_steps)) active = false;
     }
     if (a.steps_total) {
         for (int o = 16; o > 0; o >>= 1) my_steps += __shfl_down_sync(0xffffffffu, my_steps, o);
@@ -217,7 +217,7 @@ __global__ void k_debug_eval32(const DevParams *__restrict__ prm, const DevSpeci
     if (i >= n) return;
     float dbg[kDebugEvalN];
     m32::Drift c;
-    m32::eval<true, 1>(P32<1>{reinterpret_cast<const float *>(&prm[0].f)}, spc[0].aoz_m0_sq, spc[0].sgnq, (float)st[4 * i], (float)st[4 * i + 1],
+    m32::eval<true, false, 1>(P32<1>{reinterpret_cast<const float *>(&prm[0].f)}, spc[0].aoz_m0_sq, spc[0].sgnq, (float)st[4 * i], (float)st[4 * i + 1],
               (float)st[4 * i + 2], (float)st[4 * i + 3], c, dbg);
     for (int j = 0; j < kDebugEvalN; ++j) out[(size_t)i * kDebugEvalN + j] = dbg[j];
 }
@@ -227,15 +227,19 @@ __global__ void k_debug_eval32(const DevParams *__restrict__ prm, const DevSpeci
 template <int ACC, bool EN>
 static size_t pack_bytes(unsigned block) { return (size_t)block * sizeof(Packed<ACC, EN>); }
 
-// Call fn(acc, compact, energy, extended) with each flag as a compile-time constant.
+// Call fn(acc, compact, energy, extended, full) with each flag as a compile-time constant.
 template <class Fn>
 static void visit_variant(MixedVariant v, bool compact, Fn &&fn)
 {
     auto on_acc = [&](auto A) {
         auto on_compact = [&](auto C) {
             auto on_energy = [&](auto E) {
-                if (v.extended) fn(A, C, E, std::true_type{});
-                else fn(A, C, E, std::false_type{});
+                auto on_ext = [&](auto X) {
+                    if (v.full) fn(A, C, E, X, std::true_type{});
+                    else fn(A, C, E, X, std::false_type{});
+                };
+                if (v.extended) on_ext(std::true_type{});
+                else on_ext(std::false_type{});
             };
             if (v.energy) on_energy(std::true_type{});
             else on_energy(std::false_type{});
@@ -250,10 +254,11 @@ static void visit_variant(MixedVariant v, bool compact, Fn &&fn)
 int mixed_max_blocks_per_sm(MixedVariant v, unsigned block, bool compact)
 {
     int nb = 0;
-    visit_variant(v, compact, [&](auto A, auto C, auto E, auto S) {
+    visit_variant(v, compact, [&](auto A, auto C, auto E, auto S, auto F) {
         constexpr int acc = decltype(A)::value;
         constexpr bool c = decltype(C)::value, en = decltype(E)::value, sh = decltype(S)::value;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<acc, c, en, sh>, (int)block,
+        constexpr bool fu = decltype(F)::value;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate_mixed<acc, c, en, sh, fu>, (int)block,
                                                       c ? pack_bytes<acc, en>(block) : 0);
     });
     return nb;
@@ -264,10 +269,11 @@ cudaError_t launch_propagate_mixed(const LaunchArgs &a, MixedVariant v, Persiste
     if (a.n_total == 0) return cudaSuccess;
     cudaGetLastError();
     const uint32_t per = shape.compact_period;
-    visit_variant(v, per != 0, [&](auto A, auto C, auto E, auto S) {
+    visit_variant(v, per != 0, [&](auto A, auto C, auto E, auto S, auto F) {
         constexpr int acc = decltype(A)::value;
         constexpr bool c = decltype(C)::value, en = decltype(E)::value, sh = decltype(S)::value;
-        k_propagate_mixed<acc, c, en, sh><<<shape.grid, shape.block, c ? pack_bytes<acc, en>(shape.block) : 0, s>>>(
+        constexpr bool fu = decltype(F)::value;
+        k_propagate_mixed<acc, c, en, sh, fu><<<shape.grid, shape.block, c ? pack_bytes<acc, en>(shape.block) : 0, s>>>(
             a, c ? per : 1u);
     });
     note_launch();

@@ -143,7 +143,7 @@ extern "C" cosmica_status cosmica_propagate_noalloc(const cosmica_params *params
     } else {
         const unsigned block = 128;
         const MixedVariant v{params->precision, params->formulation == 1,
-                             params->n_shells > 0 || params->squashed != 0};
+                             params->n_shells > 0 || params->squashed != 0, full_model(*params)};
         const int bps = std::max(1, mixed_max_blocks_per_sm(v, block, true));
         uint64_t grid = (uint64_t)num_sms() * (uint64_t)bps;
         grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (total + block - 1) / block));

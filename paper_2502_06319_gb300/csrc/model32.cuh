@@ -116,8 +116,12 @@ __device__ __forceinline__ bool outside_squashed(const P32<ST> &q, float r, floa
 
 // EXT: the parameter sets of the launch may have radial shells or a squashed
 // heliosphere (compile-time, so that launches of the basic model carry none of
-// that code or its registers).
-template <bool EXT, uint32_t ST>
+// that code or its registers).  FULL: every set of the launch is the full model
+// (drift and current sheet on, adaptive step); the uniform branches on those
+// switches then vanish and the step is one long branch-free block, which the
+// compiler schedules with more instruction-level parallelism (the latency of a
+// lone path is what bounds the end of a launch).
+template <bool EXT, bool FULL, uint32_t ST>
 __device__ __forceinline__ void eval(const P32<ST> &q, float M2, float sq, float r, float th, float ph,
                                      float lnP, Drift &o, float *dbg = nullptr)
 {
@@ -224,7 +228,7 @@ __device__ __forceinline__ void eval(const P32<ST> &q, float M2, float sq, float
 
     // drift v_d = sgn(qA) curl(kappa_A h e_B)
     float vd0 = 0.0f, vd1 = 0.0f, vd2 = 0.0f, delta = 0.0f, h = 1.0f;
-    if (P32F(q, drift) != 0.0f) {
+    if (FULL || P32F(q, drift) != 0.0f) {
         const float r2 = r * r;
         const float F = r2 * iq;
         const float Gf = F * Gam;
@@ -232,7 +236,7 @@ __device__ __forceinline__ void eval(const P32<ST> &q, float M2, float sq, float
         const float dGf_dr = r * Gam * (3.0f + G2) * iq2;
         const float dGf_dth = r2 * dGam_dth * (1.0f - G2) * iq2;
         float hr = 0.0f, ht = 0.0f, hp = 0.0f;
-        if (P32F(q, hcs) != 0.0f) {
+        if (FULL || P32F(q, hcs) != 0.0f) {
             const float phs = fmaf(P32F(q, Omega) * r, inv_V, ph);
             const float dphs_dr = P32F(q, Omega) * inv_V;
             const float dphs_dth = -P32F(q, Omega) * r * dV * inv_V * inv_V;
@@ -248,15 +252,12 @@ __device__ __forceinline__ void eval(const P32<ST> &q, float M2, float sq, float
             const float dthcs = (ta * cp) * inv_den;
             const float sqiq = sqrtf(iq);
             const float w_rl = P32F(q, D2) * P * r * sqiq;
-            float dd_dr = 0.0f, dd_dth = 0.0f;
-            if (w_rl > P32F(q, dcs_min)) {
-                delta = w_rl;
-                const float k3 = P32F(q, D2) * P * iq * sqiq;
-                dd_dr = k3;
-                dd_dth = -k3 * r * Gam * dGam_dth;
-            } else {
-                delta = P32F(q, dcs_min);
-            }
+            // half-width max(2 r_L / r, floor) and its derivatives, by selects (no branch)
+            const bool rl = w_rl > P32F(q, dcs_min);
+            const float k3 = P32F(q, D2) * P * iq * sqiq;
+            delta = rl ? w_rl : P32F(q, dcs_min);
+            const float dd_dr = rl ? k3 : 0.0f;
+            const float dd_dth = rl ? -k3 * r * Gam * dGam_dth : 0.0f;
             const float inv_d = __fdividef(1.0f, delta);
             const float u = (th_cs - th) * inv_d;
             const float sh = half_one_plus_tanh(u);
@@ -287,13 +288,13 @@ __device__ __forceinline__ void eval(const P32<ST> &q, float M2, float sq, float
 
     // step length
     float dt;
-    if (P32F(q, dt_fixed) > 0.0f) {
+    if (!FULL && P32F(q, dt_fixed) > 0.0f) {
         dt = P32F(q, dt_fixed);
     } else {
         const float t1 = __fdividef(P32F(q, eps_adv2) * Krr, Ar_tot * Ar_tot);
         const float t2 = __fdividef(P32F(q, eps_diff) * r * r, Krr);
         dt = fminf(P32F(q, dt_max), fminf(t1, t2));
-        if (delta > 0.0f) {
+        if (FULL || delta > 0.0f) {
             const float rd = r * delta;
             dt = fminf(dt, __fdividef(P32F(q, eps_diff) * rd * rd, Ktt));
         }
