@@ -55,7 +55,8 @@ SM_LANES_PER_CLK = 128      # 4 SMSPs x 32 lanes: one warp instruction per SMSP 
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; the command is in
 # profiles/launches_bench_c2.md).  They describe the kernel built from the sources whose
 # SHA-256 is recorded; any other build reports traffic null.
-TRAFFIC_C2 = {"bytes_per_launch": None, "sources_sha256": None}
+TRAFFIC_C2 = {"bytes_per_launch": 10552832,   # 5 467 392 read + 5 085 440 written
+              "sources_sha256": "6a678731e239bee3ec31686e0fe57be3ecba896aff84108542408037d587113b"}
 KERNEL_SOURCES = ("common.cuh", "philox.cuh", "model32.cuh", "mixed_state.cuh", "k_mixed.cu")
 
 
@@ -90,7 +91,39 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--cpu-sample", type=int, default=0, help="particles per energy in the oracle sample")
+    ap.add_argument("--probe-latency", action="store_true",
+                    help="instead of the bench: the step latency of a lone path (one warp of config-1 "
+                         "protons at 0.1 GeV, so the longest of 32 paths sets the time) and of few warps")
     return ap.parse_args()
+
+
+def probe_latency(cz, torch):
+    """Step latency when few warps are resident, the regime that ends every launch: time of a
+    launch / steps of its longest path, for 32 (one warp) up to 152 x 32 x 16 particles."""
+    p = W.params()
+    b = cz.cosmica_batch_create([cz.make_params(p, cz.PREC_MIXED)], [cz.make_species(W.PROTON)])
+    stream = torch.cuda.Stream()
+    res = []
+    for n in (32, 152 * 32, 152 * 32 * 16):
+        items = cz.make_items([(0, 0, 0.1, n, 0, 11)])
+        out = cz.ExitBuffers(n)
+        steps = torch.zeros(1, dtype=torch.int64, device="cuda")
+        tune = cz.cosmica_tuning(128, 0, 0, 0, 1)
+        for _ in range(2):      # the second run is timed
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                cz.cosmica_batch_run(b, items, 1, out, tuning=tune, steps_out=steps, stream=stream)
+                e1.record(stream)
+            stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        mx = int(out.numpy()["steps"].max())
+        res.append({"particles": n, "ms": ms, "longest_path_steps": mx, "ns_per_step_of_longest": ms * 1e6 / mx,
+                    "steps_per_s": int(steps.item()) / (ms * 1e-3)})
+    cz.cosmica_batch_destroy(b)
+    print(json.dumps({"probe": "lone-path step latency, config-1 protons at 0.1 GeV, mixed precision",
+                      "runs": res}), flush=True)
 
 
 def workload(args):
@@ -271,6 +304,8 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU: the hot path has no CPU implementation")
     torch.cuda.set_device(local)
+    if args.probe_latency:
+        return probe_latency(cz, torch)
     dist = None
     if world > 1:
         import torch.distributed as dist
