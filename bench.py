@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--c3-scale", type=float, default=1.0, help="scale of config-3 particle counts")
     ap.add_argument("--scale", type=float, default=1.0, help="scale of config-1/2 particles per energy")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shape instead of the autotuner")
+    ap.add_argument("--tuning", default="", help="fixed launch shape 'block,blocks_per_sm,compact_period' "
+                                                  "instead of the autotuner")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_f64acc", "fp64"],
                     help="mixed: FP32 step with compensated FP32 (float-float) accumulation")
     ap.add_argument("--formulation", default="momentum", choices=["momentum", "energy"],
@@ -355,7 +357,10 @@ def main():
     arr = cz.make_items(items)
     nI = len(items)
     batch = make_batch(prec)
-    if args.no_autotune:
+    if args.tuning:
+        blk, bps, per = (int(x) for x in args.tuning.split(","))
+        tune = cz.cosmica_tuning(blk, bps, per, 0, 1)
+    elif args.no_autotune:
         tune = cz.cosmica_tuning(128, 0, 64, 0, 1)
     else:
         tune, tune_rate = cz.cosmica_autotune(batch, arr, nI)
