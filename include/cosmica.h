@@ -388,11 +388,14 @@ cosmica_status cosmica_batch_spectrum(cosmica_batch *batch, const cosmica_work_i
                                       void *stream);
 
 /* Pick a launch shape for this batch by timing candidate shapes (block size,
- * resident blocks, compaction period) on a sample of `items` (host) and write
- * the fastest to *best (steps/s in *best_rate if not NULL).  Results are cached
- * for the process per device and configuration class (precision, drift,
- * termination shock, particle count within a factor of two); a cached class
- * returns at once.  Synchronous; uses the batch's own scratch. */
+ * resident blocks, compaction period) and write the fastest to *best (its
+ * predicted steps/s in *best_rate if not NULL).  Batches of up to ~6 particles
+ * per resident lane are timed whole; larger ones on two scaled samples of
+ * `items` (host), from which each candidate's time for the whole batch is
+ * extrapolated linearly in the particle count.  Results are cached for the
+ * process per device and configuration class (precision, drift, termination
+ * shock, particle count within a factor of two, kernel variant); a cached
+ * class returns at once.  Synchronous; uses the batch's own scratch. */
 cosmica_status cosmica_autotune(cosmica_batch *batch, const cosmica_work_item *items,
                                 uint32_t n_items, cosmica_tuning *best, double *best_rate);
 

@@ -1033,24 +1033,37 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
     cosmica_status st = batch_items(b, items, n_items, its, pre);
     if (st != COSMICA_OK) return st;
     if (pre[n_items] == 0) return fail(COSMICA_ERR_INVALID, "autotune needs particles");
-    // sample: every item scaled down so the sample holds ~6 particles per resident lane
+    // A launch's time is about t(P) = a + b P in its particle count P: b is the cost of a
+    // particle at full occupancy, a the tail that no launch avoids (its slowest paths run
+    // alone at the end).  Small batches (up to ~6 particles per resident lane) are timed
+    // whole; larger ones on two scaled samples (~2 and ~6 per lane), from which each
+    // candidate's time for the whole batch is extrapolated.  A single small sample would
+    // over-weight the tail and favour shapes that are slower on the full batch.
     const uint64_t lanes = (uint64_t)num_sms() * 2048u;
-    const double scale = std::min(1.0, 6.0 * (double)lanes / (double)pre[n_items]);
-    std::vector<cosmica_work_item> sample(items, items + n_items);
-    uint64_t total = 0;
-    for (auto &w : sample) {
-        w.n = (uint32_t)std::ceil(w.n * scale);
-        total += w.n;
-    }
+    const uint64_t n_full = pre[n_items];
+    const double s_hi = std::min(1.0, 6.0 * (double)lanes / (double)n_full);
+    const double s_lo = std::min(1.0, 2.0 * (double)lanes / (double)n_full);
+    const bool whole = s_hi >= 1.0;
+    auto make_sample = [&](double scale, uint64_t *total) {
+        std::vector<cosmica_work_item> v(items, items + n_items);
+        *total = 0;
+        for (auto &w : v) {
+            w.n = (uint32_t)std::ceil(w.n * scale);
+            *total += w.n;
+        }
+        return v;
+    };
+    uint64_t n_hi = 0, n_lo = 0;
+    std::vector<cosmica_work_item> sample_hi = make_sample(s_hi, &n_hi);
+    std::vector<cosmica_work_item> sample_lo = make_sample(s_lo, &n_lo);
     DevBuf out_buf;
     ExitPtrs ex;
     {
         ExitStage tmp;
-        st = tmp.make(total, ex, b->params[0].formulation == 1);
+        st = tmp.make(n_hi, ex, b->params[0].formulation == 1);
         if (st != COSMICA_OK) return st;
         out_buf = tmp.buf;
     }
-    cosmica_exit_states eo{ex.r, ex.th, ex.ph, ex.lnP, ex.s, ex.steps, ex.status, ex.item, total, ex.lw};
     unsigned long long *d_steps = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1058,6 +1071,26 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    // time one run of a sample with shape t: milliseconds and steps
+    auto run = [&](const std::vector<cosmica_work_item> &smp, uint64_t n, const cosmica_tuning &t, double *ms_out,
+                   double *steps_out) -> bool {
+        cosmica_exit_states eo{ex.r, ex.th, ex.ph, ex.lnP, ex.s, ex.steps, ex.status, ex.item, n, ex.lw};
+        ce = cudaEventRecord(e0, s);
+        if (ce != cudaSuccess) return false;
+        st = cosmica_batch_run(b, smp.data(), n_items, &t, &eo, (uint64_t *)d_steps, s);
+        if (st != COSMICA_OK) return false;
+        ce = cudaEventRecord(e1, s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) return false;
+        float ms = 0.0f;
+        unsigned long long steps = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ce = cudaMemcpy(&steps, d_steps, sizeof(steps), cudaMemcpyDeviceToHost);
+        if (ce != cudaSuccess) return false;
+        *ms_out = ms;
+        *steps_out = (double)steps;
+        return true;
+    };
     double best_r = -1.0;
     cosmica_tuning bt{128, 0, 64, 0, 1};
     if (ce == cudaSuccess) {
@@ -1068,7 +1101,7 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
             for (unsigned per : periods) {
                 const unsigned maxb = (unsigned)std::max(1, mixed_max_blocks_per_sm(b->variant(), blk, per != 0));
                 // all resident blocks, one fewer, and half: fewer resident warps can win when the
-                // register file or the L1 is the contended resource
+                // register file or the L1 is the contended resource, or when the tail dominates
                 cands.push_back(cosmica_tuning{blk, maxb, per, 0, 1});
                 if (maxb >= 3) cands.push_back(cosmica_tuning{blk, maxb - 1, per, 0, 1});
                 if (maxb / 2 >= 1 && maxb / 2 != maxb && maxb / 2 != maxb - 1)
@@ -1076,19 +1109,17 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
             }
         }
         for (const cosmica_tuning &t : cands) {
-            ce = cudaEventRecord(e0, s);
-            if (ce != cudaSuccess) break;
-            st = cosmica_batch_run(b, sample.data(), n_items, &t, &eo, (uint64_t *)d_steps, s);
-            if (st != COSMICA_OK) break;
-            ce = cudaEventRecord(e1, s);
-            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-            if (ce != cudaSuccess) break;
-            float ms = 0.0f;
-            unsigned long long steps = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ce = cudaMemcpy(&steps, d_steps, sizeof(steps), cudaMemcpyDeviceToHost);
-            if (ce != cudaSuccess) break;
-            const double rate = ms > 0.0f ? (double)steps / (ms * 1e-3) : 0.0;
+            double ms_hi = 0.0, st_hi = 0.0, ms_lo = 0.0, st_lo = 0.0;
+            if (!run(sample_hi, n_hi, t, &ms_hi, &st_hi)) break;
+            double ms_pred = ms_hi, steps_pred = st_hi;
+            if (!whole) {
+                if (!run(sample_lo, n_lo, t, &ms_lo, &st_lo)) break;
+                const double slope = (ms_hi - ms_lo) / (double)(n_hi - n_lo);   // ms per particle
+                const double ratio = (double)n_full / (double)n_hi;
+                ms_pred = slope > 0.0 ? ms_hi + slope * (double)(n_full - n_hi) : ms_hi * ratio;
+                steps_pred = st_hi * ratio;
+            }
+            const double rate = ms_pred > 0.0 ? steps_pred / (ms_pred * 1e-3) : 0.0;
             if (rate > best_r) {
                 best_r = rate;
                 bt = t;
