@@ -66,7 +66,7 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
     } else {
         lnP = x.flnP();
     }
-    m32::eval<EXT, FULL, kSetsPerPage>(q, L.M2, L.sq, x.fr(), x.fth(), x.fph(), lnP, c);
+    m32::eval<EXT, FULL, kSetsPerPage>(q, L.M2, L.sq, x.fr(), x.fth(), x.sin_th(), x.fph(), lnP, c);
     const float sdt = sqrtf(c.dt);
     const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
     const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);
@@ -217,8 +217,9 @@ __global__ void k_debug_eval32(const DevParams *__restrict__ prm, const DevSpeci
     if (i >= n) return;
     float dbg[kDebugEvalN];
     m32::Drift c;
-    m32::eval<true, false, 1>(P32<1>{reinterpret_cast<const float *>(&prm[0].f)}, spc[0].aoz_m0_sq, spc[0].sgnq, (float)st[4 * i], (float)st[4 * i + 1],
-              (float)st[4 * i + 2], (float)st[4 * i + 3], c, dbg);
+    m32::eval<true, false, 1>(P32<1>{reinterpret_cast<const float *>(&prm[0].f)}, spc[0].aoz_m0_sq, spc[0].sgnq,
+                              (float)st[4 * i], (float)st[4 * i + 1], m32::sin_theta_f64(st[4 * i + 1]),
+                              (float)st[4 * i + 2], (float)st[4 * i + 3], c, dbg);
     for (int j = 0; j < kDebugEvalN; ++j) out[(size_t)i * kDebugEvalN + j] = dbg[j];
 }
 

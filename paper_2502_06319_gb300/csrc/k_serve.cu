@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
         m32::normals(S.L.seed, S.L.pid, S.L.k, z0, z1, z2);
         m32::Drift c;
         const P32<1> q{S.L.q};
-        m32::eval<false, false, 1>(q, S.L.M2, S.L.sq, x.fr(), x.fth(), x.fph(), x.flnP(), c);
+        m32::eval<false, false, 1>(q, S.L.M2, S.L.sq, x.fr(), x.fth(), x.sin_th(), x.fph(), x.flnP(), c);
         const float sdt = sqrtf(c.dt);
         const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
         const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);

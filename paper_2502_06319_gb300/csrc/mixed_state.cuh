@@ -38,6 +38,16 @@ struct Acc<COSMICA_PREC_MIXED> {
     __device__ float fth() const { return th.hi; }
     __device__ float fph() const { return ph.hi; }
     __device__ float flnP() const { return lnP.hi; }
+    // distance of theta (hi + lo, in [0, pi]) to the nearer pole, to FP32 accuracy:
+    // near pi it is formed from the float-float splits of pi and theta (the high
+    // parts subtract exactly), so it keeps its sign and relative accuracy even
+    // where the FP32 theta rounds to pi or beyond
+    __device__ float pole_distance() const
+    {
+        if (th.hi < m32::kHalfPiF) return th.hi;
+        return __fadd_rn(__fsub_rn(m32::kPiF, th.hi), __fsub_rn(m32::kPiLoF, th.lo));
+    }
+    __device__ float sin_th() const { return m32::sin_from_pole_distance(pole_distance()); }
     __device__ void add(float dr, float dth, float dph, float dlnP, float dt)
     {
         m32::ff_add(r, dr);
@@ -53,7 +63,7 @@ struct Acc<COSMICA_PREC_MIXED> {
             r.hi = -r.hi; r.lo = -r.lo;
             m32::ff_add(r, r_in2);
         }
-        if (th.hi < 0.0f || th.hi > m32::kPiF) fold_theta();
+        if (th.hi < 0.0f || pole_distance() < 0.0f) fold_theta();    // theta < 0 or theta > pi
         if (ph.hi < 0.0f || ph.hi >= m32::kTwoPiF) wrap_phi();
     }
     __device__ void fold_theta()
@@ -97,6 +107,7 @@ struct Acc<COSMICA_PREC_MIXED_F64ACC> {
     __device__ float fth() const { return (float)th; }
     __device__ float fph() const { return (float)ph; }
     __device__ float flnP() const { return (float)lnP; }
+    __device__ float sin_th() const { return m32::sin_theta_f64(th); }
     __device__ void add(float dr, float dth, float dph, float dlnP, float dt)
     {
         r += (double)dr; th += (double)dth; ph += (double)dph; lnP += (double)dlnP; s += (double)dt;

@@ -28,7 +28,8 @@ namespace cosmica {
 namespace m32 {
 
 constexpr float kHalfPiF = 1.57079632679489662f;
-constexpr float kPiF = 3.14159265358979324f;
+constexpr float kPiF = 3.14159265358979324f;          // pi rounded to FP32 (above pi)
+constexpr float kPiLoF = -8.74227766e-8f;             // pi - kPiF, rounded to FP32
 constexpr float kTwoPiF = 6.28318530717958648f;
 constexpr float kInvTwoPiF = 0.159154943091895336f;
 constexpr float kSqrt2F = 1.41421356237309505f;
@@ -114,6 +115,24 @@ __device__ __forceinline__ bool outside_squashed(const P32<ST> &q, float r, floa
     return fmaf(xa * xa, P32F(q, hp_ia2), rp2 * P32F(q, hp_ib2)) >= 1.0f;
 }
 
+// sin(theta) from the distance d to the nearer pole (d >= 0, exact to FP32).  The
+// SFU sine has an absolute, not a relative, error bound, so near a pole it can
+// return 0 (and 1/sin theta = inf): below d = 0.1 a Taylor polynomial is used,
+// d (1 - d^2/6 (1 - d^2/20)), whose truncation error is below 2e-11 relative.
+__device__ __forceinline__ float sin_from_pole_distance(float d)
+{
+    const float d2 = d * d;
+    const float taylor = d * fmaf(-d2 * 0.16666667f, fmaf(-d2, 0.05f, 1.0f), 1.0f);
+    return d < 0.1f ? taylor : __sinf(d);
+}
+
+// The same for a theta given in FP64 (the debug evaluator, FP64-accumulated states).
+__device__ __forceinline__ float sin_theta_f64(double th)
+{
+    const double d = th < 0.5 * kPi ? th : kPi - th;
+    return sin_from_pole_distance((float)d);
+}
+
 // EXT: the parameter sets of the launch may have radial shells or a squashed
 // heliosphere (compile-time, so that launches of the basic model carry none of
 // that code or its registers).  FULL: every set of the launch is the full model
@@ -121,15 +140,18 @@ __device__ __forceinline__ bool outside_squashed(const P32<ST> &q, float r, floa
 // switches then vanish and the step is one long branch-free block, which the
 // compiler schedules with more instruction-level parallelism (the latency of a
 // lone path is what bounds the end of a launch).
+// sin_th: sin(theta) accurate relative to itself near the poles (the caller derives
+// it from the compensated state, see sin_from_pole_distance); cos theta is taken
+// from the SFU, whose absolute error is harmless in cot theta.
 template <bool EXT, bool FULL, uint32_t ST>
-__device__ __forceinline__ void eval(const P32<ST> &q, float M2, float sq, float r, float th, float ph,
-                                     float lnP, Drift &o, float *dbg = nullptr)
+__device__ __forceinline__ void eval(const P32<ST> &q, float M2, float sq, float r, float th, float sin_th,
+                                     float ph, float lnP, Drift &o, float *dbg = nullptr)
 {
     const float P = __expf(lnP);
     const float beta = P * rsqrtf(fmaf(P, P, M2));
     o.beta = beta;
-    float sn, cs;
-    __sincosf(th, &sn, &cs);
+    const float sn = sin_th;
+    const float cs = __cosf(th);
     const float inv_sn = __fdividef(1.0f, sn);
     const float cot = cs * inv_sn;
     const float inv_r = __fdividef(1.0f, r);
