@@ -55,8 +55,8 @@ SM_LANES_PER_CLK = 128      # 4 SMSPs x 32 lanes: one warp instruction per SMSP 
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; the command is in
 # profiles/launches_bench_c2.md).  They describe the kernel built from the sources whose
 # SHA-256 is recorded; any other build reports traffic null.
-TRAFFIC_C2 = {"bytes_per_launch": 10552832,   # 5 467 392 read + 5 085 440 written
-              "sources_sha256": "6a678731e239bee3ec31686e0fe57be3ecba896aff84108542408037d587113b"}
+TRAFFIC_C2 = {"bytes_per_launch": 9501696,   # 5 033 728 read + 4 467 968 written
+              "sources_sha256": "c9f2f44d53e4ff1c72640565066673e130a1a193cc0ba3ecb84560db1224f3c0"}
 KERNEL_SOURCES = ("common.cuh", "philox.cuh", "model32.cuh", "mixed_state.cuh", "k_mixed.cu")
 
 
