@@ -84,7 +84,7 @@ enum {
  *           eps_diff (r delta)^2/K_th) floored at dt_min (the advective step
  *           is kept small against the diffusive one, Sec. IV.A)
  *   bounds  absorbing at r >= R_out, reflecting at r_in, theta folded at the poles
- * isotropic != 0 selects the spherically symmetric "1D model" of Sec. IV.B:
+ * isotropic != 0 selects the spherically symmetric 1-D model of Sec. IV.B:
  *   K = K0 beta P times the identity, uniform wind V_const_kms, no drift.
  * Fill with cosmica_params_default() and override; struct_size and version
  * guard the ABI.

@@ -1,6 +1,6 @@
 """Pins of the oracle's SDE integration on the spherically symmetric model.
 
-Isotropic K = K0 beta P with uniform radial wind is the "1D model" of
+Isotropic K = K0 beta P with uniform radial wind is the spherically symmetric 1-D model of
 Sec. IV.B.  Against it the oracle is pinned by results it does not compute
 itself:
   * V = 0: the process is reflected Brownian motion (generator K Laplacian).
