@@ -72,18 +72,23 @@ struct DevParams {
     F32Params f;
 };
 
-// Read-only view of one parameter set's FP32 block in a table whose consecutive
-// fields lie S floats apart (a compile-time stride, so every field is an
-// immediate offset from one per-lane pointer).  S = 1 reads one F32Params in
-// place.  The mixed kernels read the paged field-major table (S = kSetsPerPage):
-// page k holds sets 64k .. 64k+63, field f of set i at
-// k * kF32Fields * 64 + f * 64 + i % 64, so the lanes of a warp reading one
-// field of different sets touch adjacent words of at most two cache lines
-// instead of one line per set (and different L1 banks).
+// Read-only view of one parameter set's FP32 block in a table where the block's
+// fields come in quads (four consecutive fields, 16 bytes) and consecutive quads
+// lie 4 S floats apart (a compile-time stride, so every field is an immediate
+// offset from one 16-byte-aligned per-lane pointer, and the fields of a quad read
+// together can be fetched by one 16-byte load).  S = 1 reads one F32Params in
+// place.  The mixed kernels read the paged table (S = kSetsPerPage): page k holds
+// sets 64k .. 64k+63, quad g of set i at k * kF32Fields * 64 + g * 64 * 4 +
+// (i mod 64) * 4, so the lanes of a warp reading one field of different sets
+// touch a few adjacent lines instead of one line per set (and different L1 banks).
 template <uint32_t S>
 struct P32 {
-    const float *__restrict__ p;   // field 0 of the set
-    __device__ __forceinline__ float at(uint32_t field) const { return __ldg(p + field * S); }
+    const float *__restrict__ p;   // field 0 of the set, 16-byte aligned
+    __device__ __forceinline__ float at(uint32_t field) const
+    {
+        const float *__restrict__ a = static_cast<const float *>(__builtin_assume_aligned(p, 16));
+        return a[(field >> 2) * (4u * S) + (field & 3u)];
+    }
 };
 constexpr uint32_t kSetsPerPage = 64;
 #define P32F(q, m) ((q).at((uint32_t)(offsetof(F32Params, m) / sizeof(float))))
@@ -96,8 +101,9 @@ __host__ __device__ constexpr size_t f32_table_floats(uint32_t n)
 }
 __host__ __device__ constexpr size_t f32_table_offset(uint32_t i)
 {
-    return (size_t)(i / kSetsPerPage) * kF32Fields * kSetsPerPage + i % kSetsPerPage;
+    return (size_t)(i / kSetsPerPage) * kF32Fields * kSetsPerPage + (size_t)(i % kSetsPerPage) * 4;
 }
+static_assert(kF32Fields % 4 == 0, "F32Params holds whole quads");
 static_assert(sizeof(F32Params) % sizeof(float) == 0, "F32Params holds floats only");
 
 struct DevSpecies {

@@ -174,14 +174,15 @@ __global__ void k_debug_philox(uint32_t n, const uint32_t *__restrict__ ctr, uin
 // ---------------------------------------------------------------- launchers --
 static inline unsigned grid_for(uint64_t n, unsigned block) { return (unsigned)((n + block - 1) / block); }
 
-// Paged field-major copy of the FP32 blocks of n parameter sets (see P32): one
+// Paged copy of the FP32 blocks of n parameter sets in quads (see P32): one
 // thread per (set, field); the unused slots of the last page stay as they are.
 __global__ void k_f32_table(const DevParams *__restrict__ prm, uint32_t n, float *__restrict__ table)
 {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n * kF32Fields) return;
     const uint32_t i = j / kF32Fields, f = j - i * kF32Fields;
-    table[f32_table_offset(i) + (size_t)f * kSetsPerPage] = reinterpret_cast<const float *>(&prm[i].f)[f];
+    table[f32_table_offset(i) + (size_t)(f >> 2) * kSetsPerPage * 4 + (f & 3)] =
+        reinterpret_cast<const float *>(&prm[i].f)[f];
 }
 
 cudaError_t launch_f32_table(const DevParams *prm, uint32_t n, float *table, cudaStream_t s)
