@@ -55,8 +55,8 @@ SM_LANES_PER_CLK = 128      # 4 SMSPs x 32 lanes: one warp instruction per SMSP 
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; the command is in
 # profiles/launches_bench_c2.md).  They describe the kernel built from the sources whose
 # SHA-256 is recorded; any other build reports traffic null.
-TRAFFIC_C2 = {"bytes_per_launch": 9501696,   # 5 033 728 read + 4 467 968 written
-              "sources_sha256": "c9f2f44d53e4ff1c72640565066673e130a1a193cc0ba3ecb84560db1224f3c0"}
+TRAFFIC_C2 = {"bytes_per_launch": 9298176,   # 4 887 552 read + 4 410 624 written
+              "sources_sha256": "a6c707982578db0c9c3b43f0ef653237e84263566c8d3d549781281d557f7566"}
 KERNEL_SOURCES = ("common.cuh", "philox.cuh", "model32.cuh", "mixed_state.cuh", "k_mixed.cu")
 
 
