@@ -269,7 +269,8 @@ class ExitBuffers:
 
     @property
     def nbytes(self) -> int:
-        return self.n * (5 * 8 + 4 + 1 + 4)
+        """Bytes of the exit records: r, th, ph, lnP, s (f64), steps, item (u32), status (u8), lw (f64)."""
+        return self.n * (5 * 8 + 4 + 1 + 4 + (8 if self.lw is not None else 0))
 
 
 # --------------------------------------------------------------- model API --
