@@ -451,9 +451,9 @@ cosmica_status cosmica_server_create(size_t mem_budget_bytes, int32_t precision,
 
 /* Queue a request (non-blocking).  *ticket identifies it.  INVALID if the
  * request can never fit the memory budget or its fields are invalid.  The
- * server runs the momentum form of the basic heliosphere: requests with
- * formulation = 1, radial shells or a squashed heliosphere are INVALID (use
- * the batch entry points for those). */
+ * server runs the momentum form (radial shells and a squashed heliosphere
+ * included); requests with formulation = 1 are INVALID (use the batch entry
+ * points for the energy form). */
 cosmica_status cosmica_server_submit(cosmica_server *srv, const cosmica_request *req, uint64_t *ticket);
 
 /* Non-blocking: OK and *res filled (the ticket is then released) if the

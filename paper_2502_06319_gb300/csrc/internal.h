@@ -71,8 +71,8 @@ struct ServeArgs {
     uint32_t budget;               // steps per lane per quantum
 };
 
-cudaError_t launch_serve(const ServeArgs &a, int acc, PersistentShape shape, cudaStream_t s);
-int serve_max_blocks_per_sm(int acc, unsigned block);
+cudaError_t launch_serve(const ServeArgs &a, int acc, bool ext, PersistentShape shape, cudaStream_t s);
+int serve_max_blocks_per_sm(int acc, bool ext, unsigned block);
 
 void note_launch();
 

@@ -64,7 +64,9 @@ struct ServeLane {
     uint64_t exit_idx;
 };
 
-template <int ACC>
+// EXT: some resident request has radial shells or a squashed heliosphere (the
+// extended model; compile-time, as in the batched kernel).
+template <int ACC, bool EXT>
 __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
 {
     const unsigned lane = threadIdx.x & 31u;
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
         m32::normals(S.L.seed, S.L.pid, S.L.k, z0, z1, z2);
         m32::Drift c;
         const P32<1> q{S.L.q};
-        m32::eval<false, false, 1>(q, S.L.M2, S.L.sq, x.fr(), x.fth(), x.sin_th(), x.fph(), x.flnP(), c);
+        m32::eval<EXT, false, 1>(q, S.L.M2, S.L.sq, x.fr(), x.fth(), x.sin_th(), x.fph(), x.flnP(), c);
         const float sdt = sqrtf(c.dt);
         const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
         const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);
@@ -155,7 +157,8 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
 
         int status = COSMICA_PATH_RUNNING;
         if (!x.finite()) status = COSMICA_PATH_NONFINITE;
-        else if (x.exited()) status = COSMICA_PATH_EXIT;
+        else if ((EXT && P32F(q, sq) != 0.0f) ? m32::outside_squashed(q, x.fr(), x.fth(), x.fph()) : x.exited())
+            status = COSMICA_PATH_EXIT;
         else if (S.L.k >= S.L.max_steps) status = COSMICA_PATH_STEP_LIMIT;
         if (status != COSMICA_PATH_RUNNING) {
             const uint64_t g = S.exit_idx;
@@ -187,23 +190,30 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
 
 }  // namespace
 
-int serve_max_blocks_per_sm(int acc, unsigned block)
+int serve_max_blocks_per_sm(int acc, bool ext, unsigned block)
 {
     int nb = 0;
     if (acc == COSMICA_PREC_MIXED_F64ACC)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_serve<COSMICA_PREC_MIXED_F64ACC>, (int)block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ext ? k_serve<COSMICA_PREC_MIXED_F64ACC, true>
+                                                               : k_serve<COSMICA_PREC_MIXED_F64ACC, false>,
+                                                      (int)block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_serve<COSMICA_PREC_MIXED>, (int)block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ext ? k_serve<COSMICA_PREC_MIXED, true>
+                                                               : k_serve<COSMICA_PREC_MIXED, false>,
+                                                      (int)block, 0);
     return nb;
 }
 
-cudaError_t launch_serve(const ServeArgs &a, int acc, PersistentShape shape, cudaStream_t s)
+cudaError_t launch_serve(const ServeArgs &a, int acc, bool ext, PersistentShape shape, cudaStream_t s)
 {
     cudaGetLastError();
-    if (acc == COSMICA_PREC_MIXED_F64ACC)
-        k_serve<COSMICA_PREC_MIXED_F64ACC><<<shape.grid, shape.block, 0, s>>>(a);
-    else
-        k_serve<COSMICA_PREC_MIXED><<<shape.grid, shape.block, 0, s>>>(a);
+    if (acc == COSMICA_PREC_MIXED_F64ACC) {
+        if (ext) k_serve<COSMICA_PREC_MIXED_F64ACC, true><<<shape.grid, shape.block, 0, s>>>(a);
+        else k_serve<COSMICA_PREC_MIXED_F64ACC, false><<<shape.grid, shape.block, 0, s>>>(a);
+    } else {
+        if (ext) k_serve<COSMICA_PREC_MIXED, true><<<shape.grid, shape.block, 0, s>>>(a);
+        else k_serve<COSMICA_PREC_MIXED, false><<<shape.grid, shape.block, 0, s>>>(a);
+    }
     note_launch();
     return cudaGetLastError();
 }

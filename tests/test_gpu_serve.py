@@ -138,3 +138,31 @@ def test_wait_timeout_and_poll_busy():
     with pytest.raises(cz.CosmicaError):
         cz.cosmica_server_poll(srv, t, res)    # the ticket was released
     cz.cosmica_server_destroy(srv)
+
+
+def test_server_runs_extended_heliospheres_like_the_batched_path():
+    """Requests with radial shells or a squashed heliosphere, served together with a basic
+    one (the quantum then runs the extended kernel variant for all of them), give the
+    histograms of the batched path."""
+    shells = W.shell_params(W.solar_cycle_series(), rotation=60)
+    squashed = W.params(R_ts=85.0, R_out=122.0, **W.SQUASHED)
+    basic = W.config3_param_sets()[3]
+    cases = [(shells, W.PROTON, [0.3, 3.0], [120, 80], 71), (squashed, W.HELIUM4, [0.5, 5.0], [90, 60], 72),
+             (basic, W.ELECTRON, [1.0, 10.0], [70, 50], 73)]
+    srv = cz.cosmica_server_create(1 << 30, cz.PREC_MIXED, budget_steps=512)
+    res = _run(srv, [_req(p, sp, T, n, seed) for (p, sp, T, n, seed) in cases])
+    cz.cosmica_server_destroy(srv)
+    for (p, sp, T, n, seed), r in zip(cases, res):
+        job = W.Job(dict(p, max_steps=3_000_000), sp, T, n, seed, bins=W.Bins(0.1, 1000.0, 256))
+        g, out, m = gpu_run(job, precision=cz.PREC_MIXED)
+        H, J, S = gpu_spectrum(job, out)
+        m.close()
+        assert np.array_equal(r.hist, H)
+        assert np.allclose(r.J, J, rtol=1e-14, atol=0)
+
+
+def test_server_rejects_the_energy_form():
+    srv = cz.cosmica_server_create(1 << 28, cz.PREC_MIXED)
+    with pytest.raises(cz.CosmicaError):
+        cz.cosmica_server_submit(srv, _req(W.params(formulation=1.0), W.PROTON, [1.0], [10], 1))
+    cz.cosmica_server_destroy(srv)
