@@ -1114,8 +1114,8 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
             double ms_pred = ms_hi, steps_pred = st_hi;
             if (!whole) {
                 if (!run(sample_lo, n_lo, t, &ms_lo, &st_lo)) break;
-                const double slope = (ms_hi - ms_lo) / (double)(n_hi - n_lo);   // ms per particle
                 const double ratio = (double)n_full / (double)n_hi;
+                const double slope = n_hi > n_lo ? (ms_hi - ms_lo) / (double)(n_hi - n_lo) : 0.0;   // ms per particle
                 ms_pred = slope > 0.0 ? ms_hi + slope * (double)(n_full - n_hi) : ms_hi * ratio;
                 steps_pred = st_hi * ratio;
             }
