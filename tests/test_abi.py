@@ -2,11 +2,13 @@
 headers declare, and rejects malformed arguments on the host before any
 device work (no GPU needed for these paths)."""
 import ctypes as C
+import math
 import subprocess
 
 import pytest
 
 from paper_2502_06319_gb300 import cosmica as cz
+from paper_2502_06319_gb300 import workloads as W
 
 
 def test_library_exports_every_declared_symbol():
@@ -54,6 +56,38 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert L.cosmica_batch_create(None, 0, None, 0, C.byref(h)) == cz.ERR_INVALID
     assert L.cosmica_batch_run(None, None, 0, None, None, None, None) == cz.ERR_INVALID
     assert L.cosmica_debug_fn64(9, 0, None, None, None) == cz.ERR_INVALID
+
+
+def test_invalid_model_extensions_are_rejected_on_the_host():
+    """Validation of the radial shells, the squashed heliosphere, the energy form and the
+    start point happens on the host, before any device work."""
+    L = cz.lib()
+    h = C.c_void_p()
+    shells = W.shell_params(W.solar_cycle_series(), rotation=60)
+    sq = W.params(R_ts=85.0, R_out=122.0, **W.SQUASHED)
+    bad = [
+        (dict(shells, n_shells=17.0), b"n_shells"),
+        (dict(shells, shell_blend_AU=3.0), b"shell_blend"),
+        (dict(shells, shell_K0=(0.0,) * 15), b"shell_K0"),
+        (dict(shells, shell_tilt_deg=(95.0,) * 15), b"shell_tilt"),
+        (dict(sq, squashed=2.0), b"squashed"),
+        (dict(sq, hp_flank=-1.0), b"squashed"),
+        (dict(sq, r0=125.0, th0=sq["nose_th"], ph0=sq["nose_ph"]), b"outside"),
+        (W.params(formulation=2.0), b"formulation"),
+        (W.params(th0=0.0), b"th0"),
+    ]
+    for d, word in bad:
+        p = cz.make_params(d)
+        assert L.cosmica_model_create(C.byref(p), C.byref(h)) == cz.ERR_INVALID, d
+        assert word in L.cosmica_last_error(), (word, L.cosmica_last_error())
+        assert h.value is None
+    # a start point toward the tail, inside the squashed boundary, passes validation
+    # (creation then needs a GPU, so only the host check is exercised here)
+    p = cz.make_params(dict(sq, r0=125.0, th0=math.pi - sq["nose_th"], ph0=(sq["nose_ph"] + math.pi) % (2 * math.pi)))
+    st = L.cosmica_model_create(C.byref(p), C.byref(h))
+    assert st != cz.ERR_INVALID or b"outside" not in L.cosmica_last_error()
+    if h.value:
+        L.cosmica_model_destroy(h)
 
 
 def test_error_message_is_thread_local():
