@@ -37,7 +37,7 @@ def test_philox_bit_exact_vs_oracle(orc):
     t = torch()
     rng = np.random.default_rng(0)
     for key in ((1, 0), (0xDEADBEEF, 0x01234567), (0xFFFFFFFF, 0xFFFFFFFF)):
-        ctr = rng.integers(0, 2**32, size=(200_000, 4), dtype=np.uint64).astype(np.uint32)
+        ctr = rng.integers(0, 2**32, size=(340_000, 4), dtype=np.uint64).astype(np.uint32)   # > 10^6 counters in all
         ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4], [7, 0, 0, 0]]
         d_ctr = _dev(ctr.view(np.int32))
         d_out = t.empty_like(d_ctr)
