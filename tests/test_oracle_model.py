@@ -282,3 +282,17 @@ def test_full_model_reduces_to_isotropic_pathwise(orc):
     for k in ("r", "th", "lnP", "s"):
         rel = np.abs(a[k][same] - b[k][same]) / np.maximum(np.abs(a[k][same]), 1e-300)
         assert np.median(rel) < 1e-9, k
+
+
+def test_drift_sign_is_the_product_of_charge_and_polarity_signs(orc):
+    """v_d carries sgn(q) sgn(A): a proton in the A < 0 epoch and a particle of the proton's
+    mass and opposite charge in the A > 0 epoch follow the same paths, bit for bit; swapping
+    only one of the two signs changes them."""
+    anti = {"A": 1, "Z": -1, "m0": W.PROTON["m0"]}
+    T, N = [0.3, 3.0], [20, 20]
+    a = orc.run(W.params(polarity=-1.0), W.PROTON, T, N, seed=12)
+    b = orc.run(W.params(polarity=1.0), anti, T, N, seed=12)
+    for k in ("r", "th", "ph", "lnP", "s", "steps", "status"):
+        assert np.array_equal(a[k], b[k]), k
+    c = orc.run(W.params(polarity=1.0), W.PROTON, T, N, seed=12)
+    assert not np.array_equal(a["steps"], c["steps"])

@@ -183,3 +183,14 @@ def test_solar_cycle_series_and_shell_tables():
     assert p["n_shells"] == 15.0
     assert list(p["shell_K0"]) == [ser["K0"][60 - k] for k in range(15)]
     assert list(p["shell_tilt_deg"]) == [ser["tilt_deg"][60 - k] for k in range(15)]
+
+
+def test_pde_flux_form_grid_converged_with_shells():
+    # the conservative discretisation with a radially varying K converges under refinement
+    K0s = [30.0, 8.0, 20.0, 6.0, 15.0]
+    prof = lambda r: _K0_profile(r, K0s, 5, 100.0, 2.0)
+    T0 = np.array([0.3, 1.0])
+    P0 = np.sqrt(T0 * (T0 + 2 * W.PROTON["m0"]))
+    a = pde1d.solve(W.PROTON, prof, 400.0, 0.1, 100.0, 1.0, P0, n_r=800, dlnP=3e-3)
+    b = pde1d.solve(W.PROTON, prof, 400.0, 0.1, 100.0, 1.0, P0, n_r=1600, dlnP=1.5e-3)
+    assert np.all(np.abs(b / a - 1) < 2e-3), (a, b)
