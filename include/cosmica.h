@@ -212,7 +212,12 @@ void cosmica_params_default(cosmica_params *p);
 
 /* Create a model from one parameter set (host).  Validates the parameters,
  * uploads them and derives the per-set constants on the device (synchronous).
- * *out receives the handle; destroy it with cosmica_model_destroy. */
+ * *out receives the handle; destroy it with cosmica_model_destroy.
+ * Errors: INVALID (with nothing allocated) for a wrong struct_size or version,
+ * a non-positive or non-finite scale (K0, R_out, wind, field, step sizes), a
+ * non-finite angle or tolerance, a start point outside (r_in, R_out) x (0, pi)
+ * or outside the squashed outer boundary, an unknown precision or formulation,
+ * or an invalid shell table; OOM; CUDA. */
 cosmica_status cosmica_model_create(const cosmica_params *params, cosmica_model **out);
 void cosmica_model_destroy(cosmica_model *model);
 

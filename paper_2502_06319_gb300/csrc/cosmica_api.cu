@@ -97,8 +97,13 @@ cosmica_status check_params(const cosmica_params *p)
     if (outside_host(*p, p->r0_AU, p->th0_rad, p->ph0_rad))
         return fail(COSMICA_ERR_INVALID, "the start point lies outside the outer boundary");
     if (!(p->th0_rad > 0.0 && p->th0_rad < kPi)) return fail(COSMICA_ERR_INVALID, "th0 must lie in (0, pi)");
+    if (!std::isfinite(p->ph0_rad)) return fail(COSMICA_ERR_INVALID, "ph0 must be finite");
     if (!(p->dt_fixed_day > 0.0) && !(pos(p->dt_max_day) && pos(p->dt_min_day) && p->dt_min_day <= p->dt_max_day))
         return fail(COSMICA_ERR_INVALID, "need dt_fixed > 0 or 0 < dt_min <= dt_max");
+    if (std::isinf(p->dt_fixed_day)) return fail(COSMICA_ERR_INVALID, "dt_fixed must be finite");
+    if (!(p->dt_fixed_day > 0.0) && !(std::isfinite(p->eps_adv) && p->eps_adv >= 0.0 &&
+                                      std::isfinite(p->eps_diff) && p->eps_diff >= 0.0))
+        return fail(COSMICA_ERR_INVALID, "eps_adv and eps_diff must be finite and >= 0");
     if (p->max_steps < 1) return fail(COSMICA_ERR_INVALID, "max_steps must be >= 1");
     if (p->precision < COSMICA_PREC_FP64 || p->precision > COSMICA_PREC_MIXED_F64ACC)
         return fail(COSMICA_ERR_INVALID, "unknown precision %d", p->precision);
@@ -124,6 +129,8 @@ cosmica_status check_params(const cosmica_params *p)
         if (!(p->kperp_r_frac > 0.0 && p->kperp_th_frac > 0.0))
             return fail(COSMICA_ERR_INVALID, "perpendicular diffusion fractions must be > 0");
         if (p->polarity != 1 && p->polarity != -1) return fail(COSMICA_ERR_INVALID, "polarity must be +-1");
+        if (!(std::isfinite(p->lat_fast_deg) && std::isfinite(p->tilt_deg)))
+            return fail(COSMICA_ERR_INVALID, "lat_fast and tilt must be finite");
         if (p->hcs_on && !(std::fabs(p->tilt_deg) < 89.0 && pos(p->dcs_min_deg)))
             return fail(COSMICA_ERR_INVALID, "need |tilt| < 89 deg and dcs_min > 0");
         if (p->R_ts_AU > 0.0 && !(pos(p->dts_AU) && p->ts_K_factor > 0.0))

@@ -75,6 +75,11 @@ def test_invalid_model_extensions_are_rejected_on_the_host():
         (dict(sq, r0=125.0, th0=sq["nose_th"], ph0=sq["nose_ph"]), b"outside"),
         (W.params(formulation=2.0), b"formulation"),
         (W.params(th0=0.0), b"th0"),
+        (W.params(ph0=math.nan), b"ph0"),
+        (W.params(eps_adv=math.inf), b"eps_adv"),
+        (W.params(dt_fixed=math.inf), b"dt_fixed"),
+        (W.params(tilt_deg=math.nan), b"tilt"),
+        (W.params(lat_fast_deg=math.inf), b"lat_fast"),
     ]
     for d, word in bad:
         p = cz.make_params(d)
