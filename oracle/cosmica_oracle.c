@@ -34,10 +34,10 @@
  * independent 1-D PDE solver; the full-model coefficients are pinned by
  * Cartesian finite differences (Ito drift, curl, divergence), the closed-form
  * gradient-curvature drift and invariants; whole paths of the anisotropic
- * model with drifts and no current sheet (axisymmetric) are pinned by an
- * independent 2-D PDE solver.  Whole-path results of the full model with the
- * wavy current sheet are "parity unpinned" beyond those pins: no independent
- * solution exists.
+ * model with drifts, with no current sheet or a flat one (axisymmetric), are
+ * pinned by an independent 2-D PDE solver.  Whole-path results of the full
+ * model with the wavy (tilted) current sheet are "parity unpinned" beyond
+ * those pins: no independent solution exists.
  */
 #include <math.h>
 #include <stdint.h>

@@ -1,15 +1,16 @@
 """Deterministic 2-D steady transport solver for the axisymmetric heliosphere
-without a current sheet (test infrastructure only: used by tests/, never by
-the library).
+(test infrastructure only: used by tests/, never by the library).
 
 Independent whole-path check of the SDE method for the anisotropic model: the
 Parker-spiral diffusion tensor (K_par along the field, K_perp,r and K_perp,th
 across it, Eq. 2), the two-speed wind, the termination-shock factor of K, and
-the gradient-curvature drift of a unipolar field, v_d = sgn(q) sgn(A) curl(kappa_A e_B)
-with kappa_A = beta P / (3 |B|) (the drift of Eq. 1).  Without a current sheet
-none of these coefficients depends on the longitude, and neither does the
-phase-space density seen from any (r, th), so the steady momentum-form
-transport equation (Eq. 5 with df/dt = 0) reduces to (r, th):
+the drift v_d = sgn(q) sgn(A) curl(kappa_A h e_B), kappa_A = beta P / (3 |B|)
+(the drift of Eq. 1), of a unipolar field (h = 1) or of a field reversing
+across a flat current sheet (zero tilt: h = tanh((pi/2 - th) / delta),
+delta = max(2 r_L / r, delta_min), r_L = P / (c |B|)).  Then none of the
+coefficients depends on the longitude, and neither does the phase-space
+density seen from any (r, th), so the steady momentum-form transport equation
+(Eq. 5 with df/dt = 0) reduces to (r, th):
 
     div(K grad f) - (V + v_d) . grad f + (1/3) div(V) df/dlnP = 0,
     div(K grad f) = r^-2 d_r(r^2 K_rr d_r f) + (r^2 sin th)^-1 d_th(sin th K_thth d_th f),
@@ -24,17 +25,18 @@ toward lower rigidity in tau = lnP_top - lnP:
     df/dtau = (3 r / (2 V(th))) [div(K grad f) - (V + v_d) . grad f].
 
 Discretisation: finite volumes, cell faces equally spaced in ln(r + 1 AU) and
-in th; diffusive fluxes in conservative form (the Ito drift of the SDE never
-appears here: the divergence form implies it); advection by central
-differences with mirror ghosts at r_in and at the poles and the Dirichlet
-ghost 2 f_LIS - f at R_out; BDF2 in tau after one backward-Euler step.  Every
-coefficient scales with rigidity as beta P (K and kappa_A) or not at all
-(the wind), so the spatial operator is assembled once as
-S(P) = beta P S_1 + S_0 and only the linear solve is repeated per step.
+in th (optionally narrowing toward the equator); diffusive fluxes in
+conservative form (the Ito drift of the SDE never appears here: the divergence
+form implies it); advection by central differences with mirror ghosts at r_in
+and at the poles and the Dirichlet ghost 2 f_LIS - f at R_out; BDF2 in tau
+after one backward-Euler step.  K and kappa_A scale with rigidity as beta P
+and the wind not at all, so the diffusion and wind operators are assembled
+once; the drift operator too, unless a current sheet makes its width depend
+on the rigidity.
 
 The coefficients are computed here from the model's definitions (wind profile,
 spiral angle, |B| normalised at 1 AU on the equator, kappa_A converted from SI
-to AU^2/day); the drift is the curl of kappa_A e_B taken by central
+to AU^2/day); the drift is the curl of kappa_A h e_B taken by central
 differences of that analytic vector potential.  Nothing is shared with the SDE
 oracle in cosmica_oracle.c.  The modulated intensity per kinetic energy is
 J(T0) = P0^2 f(r0, th0, P0) with f_LIS = J_LIS / P^2, the quantity the Monte
@@ -52,6 +54,7 @@ AU_KM = 1.495978707e8
 AU_M = 1.495978707e11
 DAY_S = 86400.0
 DEG = math.pi / 180.0
+C_MS = 299792458.0
 
 
 def lis(T):
@@ -103,117 +106,158 @@ class _Model:
         Krr = Kpar * cos2 + self.p["kperp_r_frac"] * Kpar * (1.0 - cos2)
         return Krr, self.p["kperp_th_frac"] * Kpar
 
-    def A_ph1(self, r, th):
-        """Azimuthal component of kappa_A e_B per unit beta P [AU^2/day]; e_B = (e_r - Gam e_ph)/|..|."""
+    def polarity_h(self, r, th, P):
+        """Flat current sheet: h = tanh((pi/2 - th) / delta), delta = max(2 r_L / r, delta_min),
+        r_L = P / (c |B|); h = 1 without a sheet."""
+        if not self.p["hcs_on"]:
+            return 1.0
+        G = self.gamma(r, th)
+        rL = P * 1e9 / (C_MS * self.B0 * 1e-9 * AU_M) * r * r / np.sqrt(1.0 + G * G)
+        delta = np.maximum(2.0 * rL / r, self.p["dcs_min_deg"] * DEG)
+        return np.tanh((0.5 * math.pi - th) / delta)
+
+    def A_ph1(self, r, th, P):
+        """Azimuthal component of kappa_A h e_B per unit beta P [AU^2/day]; e_B = (e_r - Gam e_ph)/|..|."""
         G = self.gamma(r, th)
         kappa = 1e9 * DAY_S / (3.0 * self.B0 * 1e-9 * AU_M * AU_M) * r * r / np.sqrt(1.0 + G * G)
-        return -kappa * G / np.sqrt(1.0 + G * G)
+        return -kappa * self.polarity_h(r, th, P) * G / np.sqrt(1.0 + G * G)
 
-    def drift1(self, r, th):
-        """(v_r, v_th) / (beta P) of sgn(q) sgn(A) curl(kappa_A e_B) for a longitude-independent
+    def drift1(self, r, th, P):
+        """(v_r, v_th) / (beta P) of sgn(q) sgn(A) curl(kappa_A h e_B) for a longitude-independent
         potential whose th component vanishes: v_r = d_th(sin th A_ph) / (r sin th),
         v_th = -d_r(r A_ph) / r (central differences of the analytic potential)."""
         if not self.p["drift_on"]:
             z = np.zeros(np.broadcast(r, th).shape)
             return z, z
         e = 1e-5
-        vr = (np.sin(th + e) * self.A_ph1(r, th + e) - np.sin(th - e) * self.A_ph1(r, th - e)) / (2 * e)
+        vr = (np.sin(th + e) * self.A_ph1(r, th + e, P) - np.sin(th - e) * self.A_ph1(r, th - e, P)) / (2 * e)
         vr = vr / (r * np.sin(th))
         h = e * r
-        vt = -((r + h) * self.A_ph1(r + h, th) - (r - h) * self.A_ph1(r - h, th)) / (2 * h) / r
+        vt = -((r + h) * self.A_ph1(r + h, th, P) - (r - h) * self.A_ph1(r - h, th, P)) / (2 * h) / r
         return self.sign * vr, self.sign * vt
 
 
-def _grid(p, n_r, n_th):
-    a = 1.0   # AU: faces equally spaced in ln(r + a)
+def _grid(p, n_r, n_th, th_stretch=0.0):
+    """Cell faces equally spaced in ln(r + 1 AU); in th equally spaced, or, with
+    th_stretch = a > 0, th = pi/2 + (pi/2) sinh(a x) / sinh(a) for x equally spaced
+    in [-1, 1] (cells narrowest on the equator, where a current sheet lies)."""
+    a = 1.0
     s = np.linspace(math.log(p["r_in"] + a), math.log(p["R_out"] + a), n_r + 1)
     rf = np.exp(s) - a
     rf[0], rf[-1] = p["r_in"], p["R_out"]
-    tf = np.linspace(0.0, math.pi, n_th + 1)
+    if th_stretch > 0.0:
+        x = np.linspace(-1.0, 1.0, n_th + 1)
+        tf = 0.5 * math.pi + 0.5 * math.pi * np.sinh(th_stretch * x) / math.sinh(th_stretch)
+    else:
+        tf = np.linspace(0.0, math.pi, n_th + 1)
+    tf[0], tf[-1] = 0.0, math.pi
     return rf, 0.5 * (rf[1:] + rf[:-1]), tf, 0.5 * (tf[1:] + tf[:-1])
 
 
-def _operators(m, species, rf, rc, tf, tc):
-    """S_1, b_1 (per unit beta P) and S_0, b_0 of the spatial operator S f + b f_LIS."""
-    n_r, n_th = len(rc), len(tc)
-    N = n_r * n_th
-    R, r_in = rf[-1], rf[0]
-    I, J = np.meshgrid(np.arange(n_r), np.arange(n_th), indexing="ij")
-    ix = I * n_th + J
-    dcos = np.cos(tf[:-1]) - np.cos(tf[1:])
-    vol = ((rf[1:] ** 3 - rf[:-1] ** 3) / 3.0)[:, None] * dcos[None, :]
-    parts = {1: ([], [], [], np.zeros(N)), 0: ([], [], [], np.zeros(N))}
+class _Assembler:
+    """Finite-volume pieces of the spatial operator S f + b f_LIS on one grid."""
 
-    def add(which, i, j, v):
-        rows, cols, vals, _ = parts[which]
-        rows.append(np.ravel(i)); cols.append(np.ravel(j)); vals.append(np.ravel(v))
+    def __init__(self, rf, rc, tf, tc):
+        self.rf, self.rc, self.tf, self.tc = rf, rc, tf, tc
+        self.n_r, self.n_th = len(rc), len(tc)
+        self.N = self.n_r * self.n_th
+        I, J = np.meshgrid(np.arange(self.n_r), np.arange(self.n_th), indexing="ij")
+        self.ix = I * self.n_th + J
+        self.dcos = np.cos(tf[:-1]) - np.cos(tf[1:])
+        self.vol = ((rf[1:] ** 3 - rf[:-1] ** 3) / 3.0)[:, None] * self.dcos[None, :]
+        self.RC, self.TC = np.meshgrid(rc, tc, indexing="ij")
+        R, r_in = rf[-1], rf[0]
+        self.dr2 = (np.concatenate([rc[1:], [2.0 * R - rc[-1]]]) -
+                    np.concatenate([[2.0 * r_in - rc[0]], rc[:-1]]))
+        self.dt2 = (np.concatenate([tc[1:], [2.0 * math.pi - tc[-1]]]) - np.concatenate([[-tc[0]], tc[:-1]]))
 
-    def rhs(which, i, v):
-        np.add.at(parts[which][3], np.ravel(i), np.ravel(v))
+    def _new(self):
+        return [], [], [], np.zeros(self.N)
 
-    # radial diffusive fluxes through interior faces, and through R_out to the boundary value
-    Krr_f, _ = m.K1(rf[1:-1][:, None], tc[None, :])
-    a = Krr_f * (rf[1:-1] ** 2)[:, None] * dcos[None, :] / (rc[1:] - rc[:-1])[:, None]
-    lo, up = ix[:-1], ix[1:]
-    add(1, lo, up, a / vol[:-1]); add(1, lo, lo, -a / vol[:-1])
-    add(1, up, lo, a / vol[1:]); add(1, up, up, -a / vol[1:])
-    Krr_R, _ = m.K1(np.full(n_th, R), tc)
-    aR = Krr_R * R * R * dcos / (R - rc[-1])
-    last = ix[-1]
-    add(1, last, last, -aR / vol[-1]); rhs(1, last, aR / vol[-1])
-    # latitudinal diffusive fluxes (the pole faces carry none: sin th = 0)
-    _, Ktt_f = m.K1(rc[:, None], tf[1:-1][None, :])
-    ring = ((rf[1:] ** 2 - rf[:-1] ** 2) / 2.0)[:, None]
-    a = Ktt_f * np.sin(tf[1:-1])[None, :] * ring / (rc[:, None] * (tc[1:] - tc[:-1])[None, :])
-    lo, up = ix[:, :-1], ix[:, 1:]
-    add(1, lo, up, a / vol[:, :-1]); add(1, lo, lo, -a / vol[:, :-1])
-    add(1, up, lo, a / vol[:, 1:]); add(1, up, up, -a / vol[:, 1:])
-    # advection -u_r d_r f - (u_th / r) d_th f by central differences with ghosts
-    RC, TC = np.meshgrid(rc, tc, indexing="ij")
-    vr1, vt1 = m.drift1(RC, TC)
-    r_lo = np.concatenate([[2.0 * r_in - rc[0]], rc[:-1]])
-    r_hi = np.concatenate([rc[1:], [2.0 * R - rc[-1]]])
-    t_lo = np.concatenate([[-tc[0]], tc[:-1]])
-    t_hi = np.concatenate([tc[1:], [2.0 * math.pi - tc[-1]]])
-    for which, ur, ut in ((0, m.V(TC), 0.0 * TC), (1, vr1, vt1 / RC)):
-        c = -ur / (r_hi - r_lo)[:, None]            # times (f_{i+1} - f_{i-1})
-        add(which, ix[:-1], ix[1:], c[:-1]); add(which, ix[1:], ix[:-1], -c[1:])
-        add(which, ix[0], ix[0], -c[0])             # reflecting: ghost f_{-1} = f_0
-        add(which, last, last, -c[-1]); rhs(which, last, 2.0 * c[-1])   # ghost 2 f_LIS - f
-        ct = -ut / (t_hi - t_lo)[None, :]
-        add(which, ix[:, :-1], ix[:, 1:], ct[:, :-1]); add(which, ix[:, 1:], ix[:, :-1], -ct[:, 1:])
-        add(which, ix[:, 0], ix[:, 0], -ct[:, 0])    # across a pole the density is the same
-        add(which, ix[:, -1], ix[:, -1], ct[:, -1])
-    out = []
-    for which in (1, 0):
-        rows, cols, vals, b = parts[which]
-        S = sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
-        out += [S, b]
-    return out
+    @staticmethod
+    def _add(part, i, j, v):
+        part[0].append(np.ravel(i)); part[1].append(np.ravel(j)); part[2].append(np.ravel(v))
+
+    def _done(self, part):
+        rows, cols, vals, b = part
+        S = sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(self.N, self.N))
+        return S, b
+
+    def diffusion(self, K1):
+        """div(K grad f) for K = (K_rr, K_thth)(r, th) = K1(r, th): fluxes through interior faces,
+        through R_out to the boundary value, none through r_in or the poles."""
+        rf, rc, tf, tc, ix, vol, dcos = self.rf, self.rc, self.tf, self.tc, self.ix, self.vol, self.dcos
+        part = self._new()
+        Krr_f, _ = K1(rf[1:-1][:, None], tc[None, :])
+        a = Krr_f * (rf[1:-1] ** 2)[:, None] * dcos[None, :] / (rc[1:] - rc[:-1])[:, None]
+        lo, up = ix[:-1], ix[1:]
+        self._add(part, lo, up, a / vol[:-1]); self._add(part, lo, lo, -a / vol[:-1])
+        self._add(part, up, lo, a / vol[1:]); self._add(part, up, up, -a / vol[1:])
+        R = rf[-1]
+        Krr_R, _ = K1(np.full(self.n_th, R), tc)
+        aR = Krr_R * R * R * dcos / (R - rc[-1])
+        self._add(part, ix[-1], ix[-1], -aR / vol[-1])
+        np.add.at(part[3], ix[-1], aR / vol[-1])
+        _, Ktt_f = K1(rc[:, None], tf[1:-1][None, :])
+        ring = ((rf[1:] ** 2 - rf[:-1] ** 2) / 2.0)[:, None]
+        a = Ktt_f * np.sin(tf[1:-1])[None, :] * ring / (rc[:, None] * (tc[1:] - tc[:-1])[None, :])
+        lo, up = ix[:, :-1], ix[:, 1:]
+        self._add(part, lo, up, a / vol[:, :-1]); self._add(part, lo, lo, -a / vol[:, :-1])
+        self._add(part, up, lo, a / vol[:, 1:]); self._add(part, up, up, -a / vol[:, 1:])
+        return self._done(part)
+
+    def advection(self, ur, ut):
+        """-u_r d_r f - (u_th / r) d_th f for cell-centred velocities, central differences with
+        mirror ghosts at r_in and the poles and the Dirichlet ghost 2 f_LIS - f at R_out."""
+        ix = self.ix
+        part = self._new()
+        c = -ur / self.dr2[:, None]
+        self._add(part, ix[:-1], ix[1:], c[:-1]); self._add(part, ix[1:], ix[:-1], -c[1:])
+        self._add(part, ix[0], ix[0], -c[0])
+        self._add(part, ix[-1], ix[-1], -c[-1])
+        np.add.at(part[3], ix[-1], 2.0 * c[-1])
+        ct = -(ut / self.RC) / self.dt2[None, :]
+        self._add(part, ix[:, :-1], ix[:, 1:], ct[:, :-1]); self._add(part, ix[:, 1:], ix[:, :-1], -ct[:, 1:])
+        self._add(part, ix[:, 0], ix[:, 0], -ct[:, 0])
+        self._add(part, ix[:, -1], ix[:, -1], ct[:, -1])
+        return self._done(part)
 
 
-def solve(species, p, r0, th0, P0_list, n_r=80, n_th=90, dlnP=0.01, P_top=300.0):
+def solve(species, p, r0, th0, P0_list, n_r=80, n_th=90, dlnP=0.01, P_top=300.0, th_stretch=0.0):
     """Modulated J(T0) at (r0, th0) for each rigidity in P0_list (GV).
 
     p is a parameter dict with the keys of the model record (K0, kperp_r_frac,
     kperp_th_frac, B1AU_nT, V_slow_kms, V_fast_kms, lat_fast_deg, dlat_deg,
-    polarity, drift_on, R_out, R_ts, ts_K_factor, dts_AU, r_in, rot_period_day);
-    the model must be anisotropic, without a current sheet, shells or squashed
-    boundaries."""
-    if p.get("isotropic", 0.0) or p.get("hcs_on", 0.0) or p.get("n_shells", 0.0) or p.get("squashed", 0.0):
-        raise ValueError("the 2-D solver covers the axisymmetric model without a current sheet")
+    polarity, drift_on, hcs_on, tilt_deg, dcs_min_deg, R_out, R_ts, ts_K_factor,
+    dts_AU, r_in, rot_period_day); the model must be anisotropic and
+    axisymmetric: no current sheet, or a flat one (tilt 0), no shells or
+    squashed boundaries."""
+    if p.get("isotropic", 0.0) or p.get("n_shells", 0.0) or p.get("squashed", 0.0):
+        raise ValueError("the 2-D solver covers the anisotropic axisymmetric model")
+    if p.get("hcs_on", 0.0) and p.get("tilt_deg", 0.0) != 0.0:
+        raise ValueError("a tilted current sheet is not axisymmetric")
     m = _Model(p, species)
-    rf, rc, tf, tc = _grid(p, n_r, n_th)
+    rf, rc, tf, tc = _grid(p, n_r, n_th, th_stretch)
     if not (rc[0] < r0 < rc[-1] and tc[0] < th0 < tc[-1]):
         raise ValueError("the observer must lie between cell centres")
-    S1, b1, S0, b0 = _operators(m, species, rf, rc, tf, tc)
-    N = n_r * n_th
-    RC, TC = np.meshgrid(rc, tc, indexing="ij")
+    asm = _Assembler(rf, rc, tf, tc)
+    RC, TC = asm.RC, asm.TC
     M = sp.diags((3.0 * RC / (2.0 * m.V(TC))).ravel(), format="csc")
-    MS1, MS0 = M @ S1, M @ S0
-    Mb1, Mb0 = M @ b1, M @ b0
+    SK, bK = asm.diffusion(m.K1)
+    SV, bV = asm.advection(m.V(TC), 0.0 * TC)
+    MSK, MSV, MbK, MbV = M @ SK, M @ SV, M @ bK, M @ bV
+    sheet = bool(p.get("hcs_on", 0.0)) and bool(p["drift_on"])
+
+    def drift(P):
+        vr1, vt1 = m.drift1(RC, TC, P)
+        SD, bD = asm.advection(vr1, vt1)
+        return M @ SD, M @ bD
+
+    if not sheet:
+        MSD, MbD = drift(1.0)          # without a sheet the drift per beta P is rigidity-free
+    N = asm.N
     Id = sp.identity(N, format="csc")
-    # bilinear weights of the observer between cell centres
     i = int(np.searchsorted(rc, r0)) - 1
     j = int(np.searchsorted(tc, th0)) - 1
     wr = (r0 - rc[i]) / (rc[i + 1] - rc[i])
@@ -234,8 +278,10 @@ def solve(species, p, r0, th0, P0_list, n_r=80, n_th=90, dlnP=0.01, P_top=300.0)
     for n in range(n_y):
         P = math.exp(ys[n + 1])
         bP = _beta_T(species, P)[0] * P
-        L = bP * MS1 + MS0
-        src = dlnP * f_lis(species, P) * (bP * Mb1 + Mb0)
+        if sheet:
+            MSD, MbD = drift(P)
+        L = bP * (MSK + MSD) + MSV
+        src = dlnP * f_lis(species, P) * (bP * (MbK + MbD) + MbV)
         if f_prev is None:                       # backward Euler for the first step
             A, rhs = Id - dlnP * L, f + src
         else:                                    # BDF2

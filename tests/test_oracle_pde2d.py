@@ -1,12 +1,13 @@
 """Whole-path pin of the anisotropic model with drifts: the SDE oracle against an
 independent deterministic solution of the steady transport equation.
 
-Without a current sheet (unipolar field) the model is axisymmetric and the
-steady momentum-form equation (Eq. 5) is a 2-D problem in (r, th), solved by
-oracle/pde2d.py in conservative finite-volume form.  It shares no code with the
-SDE oracle: the Ito drift, the Cholesky factor, the step rule and the path
-loop of the SDE never appear in it, so a dropped or mis-signed term anywhere
-in the step (Eq. 3) changes the Monte Carlo spectrum but not the PDE's.
+With a unipolar field, or a field reversing across a flat (untilted) current
+sheet, the model is axisymmetric and the steady momentum-form equation (Eq. 5)
+is a 2-D problem in (r, th), solved by oracle/pde2d.py in conservative
+finite-volume form.  It shares no code with the SDE oracle: the Ito drift, the
+Cholesky factor, the step rule and the path loop of the SDE never appear in
+it, so a dropped or mis-signed term anywhere in the step (Eq. 3) changes the
+Monte Carlo spectrum but not the PDE's.
 """
 import json
 import math
@@ -18,7 +19,13 @@ import pytest
 from oracle import pde1d, pde2d
 from paper_2502_06319_gb300 import workloads as W
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "pde2d_unipolar.json")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "pde2d_axisymmetric.json")
+
+# coarse grids the tests solve on, and their agreement with the stored fine-grid solutions
+COARSE = {"unipolar": (dict(n_r=60, n_th=60, dlnP=0.01), 1e-3),
+          "flat_sheet": (dict(n_r=60, n_th=90, dlnP=0.02, th_stretch=1.5), 1.5e-3)}
+# paths per energy of the Monte Carlo comparison (the sheet holds paths longer: smaller steps)
+PATHS = {"unipolar": 8000, "flat_sheet": 6000}
 
 
 @pytest.fixture(scope="module")
@@ -29,6 +36,12 @@ def golden():
 
 def _P0(sp, T0):
     return np.array([sp["A"] / abs(sp["Z"]) * math.sqrt(T * (T + 2 * sp["m0"])) for T in T0])
+
+
+def _cases(golden, name):
+    cases = [c for c in golden["cases"] if c["name"] == name]
+    assert [c["params"]["polarity"] for c in cases] == [1.0, -1.0]
+    return cases
 
 
 def test_reduces_to_the_1d_solver():
@@ -42,32 +55,34 @@ def test_reduces_to_the_1d_solver():
 
 
 def test_rejects_models_outside_its_scope():
-    for extra in (dict(hcs_on=1.0), dict(isotropic=1.0)):
+    for extra in (dict(hcs_on=1.0, tilt_deg=10.0), dict(isotropic=1.0), dict(n_shells=2.0)):
         with pytest.raises(ValueError):
             pde2d.solve(W.PROTON, W.params(R_out=20.0, **extra), 1.0, 1.0, [1.0], n_r=8, n_th=8)
 
 
-def test_grid_converged(golden):
-    # a coarse grid agrees with the stored fine-grid solution (160 x 180 cells, dlnP = 0.005)
+@pytest.mark.parametrize("name", list(COARSE))
+def test_grid_converged(golden, name):
     sp = golden["species"]
     P0 = _P0(sp, golden["T0"])
     r0, th0 = golden["observer"]
-    for case in golden["cases"]:
-        J = pde2d.solve(sp, case["params"], r0, th0, P0, n_r=60, n_th=60, dlnP=0.01)
-        assert np.all(np.abs(J / np.array(case["J"]) - 1) < 1e-3), (J, case["J"])
+    grid, tol = COARSE[name]
+    for case in _cases(golden, name):
+        J = pde2d.solve(sp, case["params"], r0, th0, P0, **grid)
+        assert np.all(np.abs(J / np.array(case["J"]) - 1) < tol), (J, case["J"])
 
 
-def test_sde_spectrum_matches_pde_with_drifts(orc, golden):
-    """Both polarity epochs of the unipolar model: within 3 sigma plus 0.5 %.  The
-    allowance covers the bias of the Euler-Maruyama step and of testing for the exit
-    only after each step, 0.16-0.37 % with the default step control when measured
-    with 4e4 paths per energy (0.04-0.15 % with all step limits divided by 4), and
-    the PDE's grid error (below 3e-4)."""
+@pytest.mark.parametrize("name", list(COARSE))
+def test_sde_spectrum_matches_pde_with_drifts(orc, golden, name):
+    """Both polarity epochs: within 3 sigma plus 0.5 %.  The allowance covers the bias of
+    the Euler-Maruyama step and of testing for the exit only after each step, measured
+    with 2-4e4 paths per energy at the default step control as 0.16-0.37 % (unipolar)
+    and at most 0.25 % (flat sheet), shrinking as all step limits are divided by 4,
+    plus the PDE's grid error (below 3e-4)."""
     sp = golden["species"]
     T0 = golden["T0"]
     out = []
-    for case in golden["cases"]:
-        res = orc.run(case["params"], sp, T0, [8000] * len(T0), seed=21)
+    for case in _cases(golden, name):
+        res = orc.run(case["params"], sp, T0, [PATHS[name]] * len(T0), seed=21)
         assert np.all(res["status"] == orc.EXIT)
         J, S = orc.spectrum_unbinned(res, sp, T0)
         Jp = np.array(case["J"])
