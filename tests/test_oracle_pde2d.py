@@ -91,3 +91,16 @@ def test_sde_spectrum_matches_pde_with_drifts(orc, golden, name):
     # the drift decides: the two epochs differ by far more than their errors
     (Ja, Sa), (Jb, Sb) = out
     assert np.all(np.abs(Ja - Jb) > 10.0 * (Sa + Sb)), (Ja, Jb)
+
+
+def test_energy_form_matches_pde_with_drifts(orc, golden):
+    """The energy formulation (Eq. 1 with the loss weight of Eq. 4) meets the same bar
+    against the same PDE solutions (unipolar field, both epochs)."""
+    sp = golden["species"]
+    T0 = golden["T0"]
+    for case in _cases(golden, "unipolar"):
+        p = dict(case["params"], formulation=1.0)
+        res = orc.run(p, sp, T0, [PATHS["unipolar"]] * len(T0), seed=21)
+        J, S = orc.spectrum_energy_form(res, sp, T0)
+        Jp = np.array(case["J"])
+        assert np.all(np.abs(J - Jp) < 3.0 * S + 0.005 * Jp), (case["params"]["polarity"], J, Jp, S)
