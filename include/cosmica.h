@@ -308,7 +308,10 @@ cosmica_status cosmica_propagate_noalloc(const cosmica_params *params, const cos
  *   T_in_GeVn      host [n_energies]
  *   J_out, sigma_out  device [n_energies] (NaN where N = 0)
  *   hist_out       device [n_energies * (nbins + 3)], overwritten
- * The histogram is integer and order-independent, hence deterministic. */
+ * The histogram is integer and order-independent, hence deterministic.
+ * Errors: INVALID (NULL species/bins/outputs, P_min <= 0 or P_max <= P_min,
+ * nbins = 0, exit or outputs not in device memory, a malformed LIS table),
+ * OOM, CUDA.  n_energies = 0 is a no-op. */
 cosmica_status cosmica_spectrum(const cosmica_exit_states *exit, const cosmica_species *species,
                                 const double *T_in_GeVn, uint32_t n_energies,
                                 const cosmica_lis *lis, const cosmica_bins *bins,
@@ -326,7 +329,10 @@ cosmica_status cosmica_spectrum(const cosmica_exit_states *exit, const cosmica_s
  *                 after those of energies 0..e-1 (the order cosmica_propagate writes)
  *   n_per_energy  host [n_energies]
  *   J_out, sigma_out  device [n_energies] (NaN where N = 0)
- * Sums are reduced in a fixed order, so the result is deterministic. */
+ * Sums are reduced in a fixed order, so the result is deterministic.
+ * Errors: INVALID (NULL arguments, formulation not 0 or 1, exit->n not the sum
+ * of n_per_energy, no exit->lw for formulation 1, buffers not in device
+ * memory, a malformed LIS table), OOM, CUDA.  n_energies = 0 is a no-op. */
 cosmica_status cosmica_spectrum_unbinned(const cosmica_exit_states *exit, const cosmica_species *species,
                                          const double *T_in_GeVn, uint32_t n_energies,
                                          const uint32_t *n_per_energy, int32_t formulation,
@@ -369,7 +375,10 @@ typedef struct cosmica_batch cosmica_batch;
 
 /* Upload n_params parameter sets and n_species species (host) and derive
  * their constants on the device.  All sets must share one precision (taken
- * from params[0].precision). */
+ * from params[0].precision) and one formulation.  *out receives the handle;
+ * destroy it with cosmica_batch_destroy.  Errors: INVALID (no sets or species,
+ * a set or species rejected as by cosmica_model_create, mixed precisions or
+ * formulations; nothing allocated), OOM, CUDA. */
 cosmica_status cosmica_batch_create(const cosmica_params *params, uint32_t n_params,
                                     const cosmica_species *species, uint32_t n_species,
                                     cosmica_batch **out);
@@ -385,7 +394,8 @@ cosmica_status cosmica_batch_run(cosmica_batch *batch, const cosmica_work_item *
 
 /* Histogram and spectrum per work item of a batch run (same estimator as
  * cosmica_spectrum; item k uses its own species and energy).  J_out,
- * sigma_out: device [n_items]; hist_out: device [n_items * (nbins + 3)]. */
+ * sigma_out: device [n_items]; hist_out: device [n_items * (nbins + 3)].
+ * Errors: as cosmica_spectrum, and INVALID for a species index out of range. */
 cosmica_status cosmica_batch_spectrum(cosmica_batch *batch, const cosmica_work_item *items,
                                       uint32_t n_items, const cosmica_exit_states *exit,
                                       const cosmica_lis *lis, const cosmica_bins *bins,
@@ -400,7 +410,9 @@ cosmica_status cosmica_batch_spectrum(cosmica_batch *batch, const cosmica_work_i
  * extrapolated linearly in the particle count.  Results are cached for the
  * process per device and configuration class (precision, drift, termination
  * shock, particle count within a factor of two, kernel variant); a cached
- * class returns at once.  Synchronous; uses the batch's own scratch. */
+ * class returns at once.  Synchronous; uses the batch's own scratch.  An FP64
+ * batch needs no tuning and gets block 128 without compaction.  Errors:
+ * INVALID (NULL batch/best, invalid items, no particles), OOM, CUDA. */
 cosmica_status cosmica_autotune(cosmica_batch *batch, const cosmica_work_item *items,
                                 uint32_t n_items, cosmica_tuning *best, double *best_rate);
 
@@ -462,13 +474,15 @@ cosmica_status cosmica_server_create(size_t mem_budget_bytes, int32_t precision,
 cosmica_status cosmica_server_submit(cosmica_server *srv, const cosmica_request *req, uint64_t *ticket);
 
 /* Non-blocking: OK and *res filled (the ticket is then released) if the
- * request is finished; BUSY if not yet; INVALID for an unknown ticket. */
+ * request is finished; BUSY if not yet; INVALID for an unknown ticket; CUDA if
+ * the server failed (its message in cosmica_last_error). */
 cosmica_status cosmica_server_poll(cosmica_server *srv, uint64_t ticket, cosmica_result *res);
 
 /* As poll, waiting at most timeout_ms; TIMEOUT if still not finished. */
 cosmica_status cosmica_server_wait(cosmica_server *srv, uint64_t ticket, uint32_t timeout_ms,
                                    cosmica_result *res);
 
+/* Counters of the server so far (host copy).  Errors: INVALID (NULL arguments). */
 cosmica_status cosmica_server_stats_get(cosmica_server *srv, cosmica_server_stats *st);
 
 /* Stop the scheduler (finishing the current quantum), free everything. */

@@ -5,7 +5,9 @@
  * functions, the coefficient evaluators) so that each can be compared with
  * an independent implementation.  Same conventions as cosmica.h: device
  * pointers, stream-ordered, cosmica_status return, message via
- * cosmica_last_error().
+ * cosmica_last_error().  Errors of every probe: INVALID for a NULL handle,
+ * species or array (with n > 0) or an unknown function code, CUDA when the
+ * launch fails; n = 0 launches nothing.
  */
 #ifndef COSMICA_DEBUG_H
 #define COSMICA_DEBUG_H
