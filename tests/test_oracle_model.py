@@ -296,3 +296,21 @@ def test_drift_sign_is_the_product_of_charge_and_polarity_signs(orc):
         assert np.array_equal(a[k], b[k]), k
     c = orc.run(W.params(polarity=1.0), W.PROTON, T, N, seed=12)
     assert not np.array_equal(a["steps"], c["steps"])
+
+
+def test_units_against_hand_worked_values(orc):
+    """Hand-worked numbers (to the digits quoted): a 1 GeV proton has P = 1.696038 GV and
+    beta = 0.875026; 400 and 760 km/s are 0.231019 and 0.438937 AU/day; the spiral at 1 AU on
+    the equator has Gamma = (2 pi / 25.38 d) / 0.231019 AU/d = 1.0716; kappa_A = beta P / (3 |B|)
+    for beta P = 1 GV and |B| = 5 nT is 6.667e16 m^2/s = 0.25738 AU^2/day."""
+    P = float(orc.rigidity(W.PROTON, 1.0))
+    assert abs(P - 1.696038) < 5e-7 and abs(float(orc.beta(W.PROTON, P)) - 0.875026) < 5e-7
+    p = W.params(hcs_on=0.0)
+    e = orc.evaluate(p, W.PROTON, 1.0, math.pi / 2, 0.0, math.log(P))
+    assert abs(e["V"] - 0.231019) < 5e-7
+    assert abs(orc.evaluate(p, W.PROTON, 1.0, 0.01, 0.0, 0.0)["V"] - 0.438937) < 5e-7
+    assert abs(e["Gam"] - 1.0716) < 5e-5
+    assert abs(e["Bmag"] - 5.0) < 1e-12
+    # |kappa_A h e_B| with h = 1 at 1 AU on the equator, per GV of beta P
+    kA = math.hypot(e["Wr"], e["Wph"]) / (e["beta"] * e["P"])
+    assert abs(kA - 0.25738) < 5e-5
