@@ -29,8 +29,8 @@ def _golden():
 @pytest.mark.parametrize("precision", [cz.PREC_MIXED, cz.PREC_MIXED_F64ACC], ids=["mixed", "f64acc"])
 def test_mixed_spectrum_matches_pde(k, precision):
     g = _golden()
-    case = g["cases"][k]
-    job = W.Job(case["params"], g["species"], list(g["T0"]), [20000] * len(g["T0"]), seed=77)
+    case = [c for c in g["cases"] if c["species_name"] == "proton"][k]
+    job = W.Job(case["params"], case["species"], list(g["T0"]), [20000] * len(g["T0"]), seed=77)
     res, out, m = gpu_run(job, precision=precision)
     m.close()
     assert np.all(res["status"] == 1), np.bincount(res["status"])

@@ -38,8 +38,8 @@ def _P0(sp, T0):
     return np.array([sp["A"] / abs(sp["Z"]) * math.sqrt(T * (T + 2 * sp["m0"])) for T in T0])
 
 
-def _cases(golden, name):
-    cases = [c for c in golden["cases"] if c["name"] == name]
+def _cases(golden, name, species="proton"):
+    cases = [c for c in golden["cases"] if c["name"] == name and c["species_name"] == species]
     assert [c["params"]["polarity"] for c in cases] == [1.0, -1.0]
     return cases
 
@@ -62,12 +62,10 @@ def test_rejects_models_outside_its_scope():
 
 @pytest.mark.parametrize("name", list(COARSE))
 def test_grid_converged(golden, name):
-    sp = golden["species"]
-    P0 = _P0(sp, golden["T0"])
     r0, th0 = golden["observer"]
     grid, tol = COARSE[name]
     for case in _cases(golden, name):
-        J = pde2d.solve(sp, case["params"], r0, th0, P0, **grid)
+        J = pde2d.solve(case["species"], case["params"], r0, th0, _P0(case["species"], golden["T0"]), **grid)
         assert np.all(np.abs(J / np.array(case["J"]) - 1) < tol), (J, case["J"])
 
 
@@ -78,10 +76,10 @@ def test_sde_spectrum_matches_pde_with_drifts(orc, golden, name):
     with 2-4e4 paths per energy at the default step control as 0.16-0.37 % (unipolar)
     and at most 0.25 % (flat sheet), shrinking as all step limits are divided by 4,
     plus the PDE's grid error (below 3e-4)."""
-    sp = golden["species"]
     T0 = golden["T0"]
     out = []
     for case in _cases(golden, name):
+        sp = case["species"]
         res = orc.run(case["params"], sp, T0, [PATHS[name]] * len(T0), seed=21)
         assert np.all(res["status"] == orc.EXIT)
         J, S = orc.spectrum_unbinned(res, sp, T0)
@@ -96,11 +94,28 @@ def test_sde_spectrum_matches_pde_with_drifts(orc, golden, name):
 def test_energy_form_matches_pde_with_drifts(orc, golden):
     """The energy formulation (Eq. 1 with the loss weight of Eq. 4) meets the same bar
     against the same PDE solutions (unipolar field, both epochs)."""
-    sp = golden["species"]
     T0 = golden["T0"]
     for case in _cases(golden, "unipolar"):
+        sp = case["species"]
         p = dict(case["params"], formulation=1.0)
         res = orc.run(p, sp, T0, [PATHS["unipolar"]] * len(T0), seed=21)
         J, S = orc.spectrum_energy_form(res, sp, T0)
         Jp = np.array(case["J"])
         assert np.all(np.abs(J - Jp) < 3.0 * S + 0.005 * Jp), (case["params"]["polarity"], J, Jp, S)
+
+
+def test_other_species_match_pde(orc, golden):
+    """He-4 (A/Z = 2) and electrons (negative charge, beta ~ 1) with the unipolar field, both
+    epochs, within 3 sigma plus 0.5 %; the drift's sign follows sgn(q) sgn(A), so the epoch
+    that favours protons disfavours electrons."""
+    T0 = golden["T0"]
+    for species in ("he4", "electron"):
+        J_by_pol = {}
+        for case in _cases(golden, "unipolar", species):
+            res = orc.run(case["params"], case["species"], T0, [PATHS["unipolar"]] * len(T0), seed=21)
+            J, S = orc.spectrum_unbinned(res, case["species"], T0)
+            Jp = np.array(case["J"])
+            assert np.all(np.abs(J - Jp) < 3.0 * S + 0.005 * Jp), (species, case["params"]["polarity"], J, Jp, S)
+            J_by_pol[case["params"]["polarity"]] = Jp
+        favoured = J_by_pol[1.0] > J_by_pol[-1.0]
+        assert np.all(favoured) if species == "he4" else not np.any(favoured), (species, J_by_pol)
