@@ -122,3 +122,34 @@ def test_oracle_and_library_share_no_code():
     for f in ("cosmica.py", "_build.py", "__init__.py", "workloads.py"):
         txt = open(os.path.join(root, "paper_2502_06319_gb300", f)).read()
         assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding mirrors has the size and field offsets the C compiler gives
+    the header's declaration (a plain C program compiled with gcc against include/)."""
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = {"cosmica_params": cz.cosmica_params, "cosmica_species": cz.cosmica_species,
+               "cosmica_exit_states": cz.cosmica_exit_states, "cosmica_lis": cz.cosmica_lis,
+               "cosmica_bins": cz.cosmica_bins, "cosmica_work_item": cz.cosmica_work_item,
+               "cosmica_position": cz.cosmica_position, "cosmica_tuning": cz.cosmica_tuning,
+               "cosmica_request": cz.cosmica_request, "cosmica_result": cz.cosmica_result,
+               "cosmica_server_stats": cz.cosmica_server_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cosmica.h"', "int main(void) {"]
+    for name, py in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(root, "include"), "-o", str(exe), str(src)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        s, f, v = ln.split()
+        got[(s, f)] = int(v)
+    for name, py in structs.items():
+        assert got[(name, "size")] == C.sizeof(py), name
+        for f, _ in py._fields_:
+            assert got[(name, f)] == getattr(py, f).offset, (name, f)
