@@ -24,6 +24,14 @@
  *   - Particle identity: quasi-particle i of a work item has pid =
  *     first_pid + i.  Its Philox stream is keyed by (seed, pid, step) only, so
  *     results do not depend on batching, ordering or launch shape.
+ *   - Threads: a model or batch handle holds per-call scratch, so calls on one
+ *     handle must not overlap in time (serialise them, or give each thread
+ *     its own handle); calls on different handles may run concurrently.  A
+ *     server handle may be used from any number of threads.  Consecutive
+ *     calls on one handle on different streams must be ordered by the caller
+ *     (an event or a synchronisation): the later call reuses the handle's
+ *     device scratch that the earlier call's kernels may still read.  On one
+ *     stream they are ordered already.
  */
 #ifndef COSMICA_H
 #define COSMICA_H
