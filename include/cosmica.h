@@ -27,7 +27,8 @@
  *   - Threads: a model or batch handle holds per-call scratch, so calls on one
  *     handle must not overlap in time (serialise them, or give each thread
  *     its own handle); calls on different handles may run concurrently.  A
- *     server handle may be used from any number of threads.  Consecutive
+ *     server handle may be used from any number of threads (cosmica_server_destroy
+ *     excepted: no other call on it may be in progress).  Consecutive
  *     calls on one handle on different streams must be ordered by the caller
  *     (an event or a synchronisation): the later call reuses the handle's
  *     device scratch that the earlier call's kernels may still read.  On one
