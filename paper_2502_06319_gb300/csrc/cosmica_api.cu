@@ -337,16 +337,18 @@ std::vector<uint32_t> cost_order(const std::vector<DevItem> &its, const cosmica_
     return order;
 }
 
-int g_num_sms = 0;
+std::atomic<int> g_num_sms{0};
 int num_sms()
 {
-    if (g_num_sms == 0) {
+    int n = g_num_sms.load(std::memory_order_relaxed);
+    if (n == 0) {   // concurrent first calls all store the same value
         int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_num_sms <= 0) g_num_sms = 1;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+        g_num_sms.store(n, std::memory_order_relaxed);
     }
-    return g_num_sms;
+    return n;
 }
 
 PersistentShape shape_for(MixedVariant v, const cosmica_tuning *t, uint64_t n_total)
