@@ -292,13 +292,22 @@ cosmica_status cosmica_propagate_orbit(cosmica_model *model, const cosmica_speci
  * call (parameter block, species, work items, prefix sums, queue cursor,
  * step counter) is a fixed static device array of about 95 KB that every GPU
  * loading the library holds until the process exits; the call makes no
- * cudaMalloc, cudaFree or other allocating call.
+ * cudaMalloc, cudaFree or other allocating call.  The tables reach the array
+ * as kernel parameters, in chunks built in a few KB of the calling thread's
+ * stack (no host copies, no large stack frame).
  *   n_energies   at most COSMICA_NOALLOC_MAX_ENERGIES (INVALID otherwise)
  *   out          device memory only (INVALID otherwise)
- * The first call on a device looks the array up (cudaGetSymbolAddress with
- * that device current): make it before any stream capture.  All calls share
- * the array -- the counters are cleared at the start of each call, the tables
- * overwritten -- so calls whose work overlaps on the GPU race; serialise them.
+ * Set-up: each call whose stream is not capturing looks the array's address up
+ * (cudaGetSymbolAddress with the device current), so calls after a re-created
+ * context (cudaDeviceReset) find the new array; a call on a capturing stream
+ * uses the address of the last earlier call on that device (INVALID if there
+ * was none).  So make a first call on each device before any stream capture;
+ * that first call may also make the CUDA driver load the library's device
+ * code (lazy module loading), which allocates on the driver's side, so make
+ * it during set-up, before the phase that must not allocate.
+ * All calls share the array -- the counters are cleared at the start of each
+ * call, the tables overwritten -- so calls whose work overlaps on the GPU
+ * race; serialise them.
  */
 #define COSMICA_NOALLOC_MAX_ENERGIES 1024u
 cosmica_status cosmica_propagate_noalloc(const cosmica_params *params, const cosmica_species *species,
@@ -357,7 +366,10 @@ typedef struct {
     uint32_t species_idx;     /* into the batch's species        */
     double T_GeVn;
     uint32_t n;
-    uint32_t reserved;
+    uint32_t exit_item_plus1; /* 0: the item's exit records carry its index in
+                                 `items`; k > 0: they carry k - 1 (a shard of a
+                                 larger item list keeps that list's numbering, so
+                                 its histogram rows are the list's rows)          */
     uint64_t first_pid;
     uint64_t seed;
     double r0_AU;             /* start position of the item's particles (a detection  */
@@ -410,6 +422,22 @@ cosmica_status cosmica_batch_spectrum(cosmica_batch *batch, const cosmica_work_i
                                       const cosmica_lis *lis, const cosmica_bins *bins,
                                       double *J_out, double *sigma_out, uint64_t *hist_out,
                                       void *stream);
+
+/* Spectra of work items from a given histogram instead of exit states: the
+ * estimator of cosmica_spectrum applied to hist [n_items * (nbins + 3)]
+ * (device, the layout cosmica_batch_spectrum writes), item k with its own
+ * species and energy.  This is the last step of a workload partitioned over
+ * several GPUs (the paper distributes energy bins over GPUs and collects
+ * their histograms, Sec. IV.A): every GPU bins its share of the particles into
+ * the rows of the whole item list (cosmica_work_item.exit_item_plus1), the
+ * histograms are summed across GPUs (an all-reduce of integers, exact), and
+ * this call turns the sum into spectra, equal bit for bit to the one-GPU
+ * result.  J_out, sigma_out: device [n_items].  Errors: as
+ * cosmica_batch_spectrum (hist must be device memory). */
+cosmica_status cosmica_batch_spectrum_hist(cosmica_batch *batch, const cosmica_work_item *items,
+                                           uint32_t n_items, const cosmica_lis *lis, const cosmica_bins *bins,
+                                           const uint64_t *hist, double *J_out, double *sigma_out,
+                                           void *stream);
 
 /* Pick a launch shape for this batch by timing candidate shapes (block size,
  * resident blocks, compaction period) and write the fastest to *best (its

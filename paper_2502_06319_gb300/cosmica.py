@@ -68,7 +68,8 @@ class cosmica_bins(C.Structure):
 
 class cosmica_work_item(C.Structure):
     _fields_ = [("param_idx", C.c_uint32), ("species_idx", C.c_uint32), ("T_GeVn", C.c_double),
-                ("n", C.c_uint32), ("reserved", C.c_uint32), ("first_pid", C.c_uint64), ("seed", C.c_uint64),
+                ("n", C.c_uint32), ("exit_item_plus1", C.c_uint32), ("first_pid", C.c_uint64),
+                ("seed", C.c_uint64),
                 ("r0_AU", C.c_double), ("th0_rad", C.c_double), ("ph0_rad", C.c_double)]
 
 
@@ -138,6 +139,8 @@ def lib():
             L.cosmica_batch_spectrum.argtypes = [P, C.POINTER(cosmica_work_item), C.c_uint32,
                                                  C.POINTER(cosmica_exit_states), C.POINTER(cosmica_lis),
                                                  C.POINTER(cosmica_bins), P, P, P, P]
+            L.cosmica_batch_spectrum_hist.argtypes = [P, C.POINTER(cosmica_work_item), C.c_uint32,
+                                                      C.POINTER(cosmica_lis), C.POINTER(cosmica_bins), P, P, P, P]
             L.cosmica_autotune.argtypes = [P, C.POINTER(cosmica_work_item), C.c_uint32, C.POINTER(cosmica_tuning),
                                            C.POINTER(C.c_double)]
             L.cosmica_propagate_noalloc.argtypes = [C.POINTER(cosmica_params), C.POINTER(cosmica_species),
@@ -165,7 +168,7 @@ def lib():
             L.cosmica_debug_fn64.argtypes = [C.c_int32, C.c_uint32, P, P, P]
             L.cosmica_debug_eval.argtypes = [P, C.POINTER(cosmica_species), C.c_int32, C.c_uint32, P, P, P]
             for name in ("cosmica_model_create", "cosmica_propagate", "cosmica_spectrum", "cosmica_batch_create",
-                         "cosmica_batch_run", "cosmica_batch_spectrum", "cosmica_autotune", "cosmica_debug_philox",
+                         "cosmica_batch_run", "cosmica_batch_spectrum", "cosmica_batch_spectrum_hist", "cosmica_autotune", "cosmica_debug_philox",
                          "cosmica_debug_curand_philox", "cosmica_debug_normals64", "cosmica_debug_fn64",
                          "cosmica_debug_eval"):
                 getattr(L, name).restype = s
@@ -355,15 +358,17 @@ def cosmica_spectrum_unbinned(exit: ExitBuffers, species: cosmica_species, T_in:
 
 
 # --------------------------------------------------------------- batch API --
-def make_items(items) -> "C.Array":
+def make_items(items, exit_items=None) -> "C.Array":
     """items: iterable of (param_idx, species_idx, T, n, first_pid, seed[, (r0, th0, ph0)]);
-    without the start position the parameter set's is used."""
+    without the start position the parameter set's is used.  exit_items: optional
+    item number each item's exit records carry (default: its index in `items`)."""
     items = list(items)
     arr = (cosmica_work_item * max(1, len(items)))()
     for i, it in enumerate(items):
         pi, si, T, n, fp, sd = it[:6]
-        r0, th0, ph0 = it[6] if len(it) > 6 else (0.0, 0.0, 0.0)
-        arr[i] = cosmica_work_item(int(pi), int(si), float(T), int(n), 0, int(fp), int(sd),
+        r0, th0, ph0 = it[6] if len(it) > 6 and it[6] is not None else (0.0, 0.0, 0.0)
+        tag = 0 if exit_items is None else int(exit_items[i]) + 1
+        arr[i] = cosmica_work_item(int(pi), int(si), float(T), int(n), tag, int(fp), int(sd),
                                    float(r0), float(th0), float(ph0))
     return arr
 
@@ -391,6 +396,13 @@ def cosmica_batch_spectrum(batch: int, items, n_items: int, exit: ExitBuffers, b
     lp = C.byref(lis) if lis is not None else None
     _check(lib().cosmica_batch_spectrum(batch, items, n_items, C.byref(exit.c), lp, C.byref(bins), _ptr(J),
                                         _ptr(sigma), _ptr(hist), _stream(stream)))
+
+
+def cosmica_batch_spectrum_hist(batch: int, items, n_items: int, bins: cosmica_bins, hist, J, sigma,
+                                lis: Optional[cosmica_lis] = None, stream=None) -> None:
+    lp = C.byref(lis) if lis is not None else None
+    _check(lib().cosmica_batch_spectrum_hist(batch, items, n_items, lp, C.byref(bins), _ptr(hist), _ptr(J),
+                                             _ptr(sigma), _stream(stream)))
 
 
 def cosmica_autotune(batch: int, items, n_items: int):

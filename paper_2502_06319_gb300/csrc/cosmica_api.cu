@@ -337,16 +337,20 @@ std::vector<uint32_t> cost_order(const std::vector<DevItem> &its, const cosmica_
     return order;
 }
 
-std::atomic<int> g_num_sms{0};
+// SM count of each device ordinal, looked up on first use (a process may drive
+// GPUs with different SM counts; concurrent first calls store the same value)
+constexpr int kMaxSmDevices = 64;
+std::atomic<int> g_num_sms[kMaxSmDevices];
 int num_sms()
 {
-    int n = g_num_sms.load(std::memory_order_relaxed);
-    if (n == 0) {   // concurrent first calls all store the same value
-        int dev = 0;
-        cudaGetDevice(&dev);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::atomic<int> *slot = (dev >= 0 && dev < kMaxSmDevices) ? &g_num_sms[dev] : nullptr;
+    int n = slot ? slot->load(std::memory_order_relaxed) : 0;
+    if (n == 0) {
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (n <= 0) n = 1;
-        g_num_sms.store(n, std::memory_order_relaxed);
+        if (slot) slot->store(n, std::memory_order_relaxed);
     }
     return n;
 }
@@ -666,6 +670,10 @@ static cosmica_status upload_lis(const cosmica_lis *lis, DevBuf &buf, Staging &s
     return COSMICA_OK;
 }
 
+static cosmica_status spectrum_of_hist(const std::vector<SpecItem> &its, const cosmica_lis *lis, uint32_t nbins,
+                                       double x_lo, double dx, const uint64_t *hist, double *J, double *sigma,
+                                       DevBuf &ibuf, Staging &istage, DevBuf &lbuf, Staging &lstage, cudaStream_t s);
+
 static cosmica_status run_spectrum(const cosmica_exit_states *ex, const std::vector<SpecItem> &its,
                                    const cosmica_lis *lis, const cosmica_bins *bins, double *J, double *sigma,
                                    uint64_t *hist, DevBuf &ibuf, Staging &istage, DevBuf &lbuf, Staging &lstage,
@@ -687,7 +695,16 @@ static cosmica_status run_spectrum(const cosmica_exit_states *ex, const std::vec
     cudaError_t e = launch_histogram(exit_ptrs(ex), ex->n, n_items, bins->nbins, x_lo, dx,
                                      (unsigned long long *)hist, s);
     if (e != cudaSuccess) return cuda_fail(e, "histogram kernel launch");
-    st = ibuf.reserve(n_items * sizeof(SpecItem));
+    return spectrum_of_hist(its, lis, bins->nbins, x_lo, dx, hist, J, sigma, ibuf, istage, lbuf, lstage, s);
+}
+
+// Eq. 4 per item from a histogram already in device memory (the second half of run_spectrum).
+static cosmica_status spectrum_of_hist(const std::vector<SpecItem> &its, const cosmica_lis *lis, uint32_t nbins,
+                                       double x_lo, double dx, const uint64_t *hist, double *J, double *sigma,
+                                       DevBuf &ibuf, Staging &istage, DevBuf &lbuf, Staging &lstage, cudaStream_t s)
+{
+    const uint32_t n_items = (uint32_t)its.size();
+    cosmica_status st = ibuf.reserve(n_items * sizeof(SpecItem));
     if (st != COSMICA_OK) return st;
     st = istage.reserve(n_items * sizeof(SpecItem));
     if (st != COSMICA_OK) return st;
@@ -697,8 +714,8 @@ static cosmica_status run_spectrum(const cosmica_exit_states *ex, const std::vec
     int kind; const double *lnT, *lnJ; uint32_t ln;
     st = upload_lis(lis, lbuf, lstage, s, &kind, &lnT, &lnJ, &ln);
     if (st != COSMICA_OK) return st;
-    e = launch_spectrum((const unsigned long long *)hist, n_items, bins->nbins, x_lo, dx, (const SpecItem *)ibuf.d,
-                        kind, lnT, lnJ, ln, J, sigma, s);
+    cudaError_t e = launch_spectrum((const unsigned long long *)hist, n_items, nbins, x_lo, dx,
+                                    (const SpecItem *)ibuf.d, kind, lnT, lnJ, ln, J, sigma, s);
     if (e != cudaSuccess) return cuda_fail(e, "spectrum kernel launch");
     return COSMICA_OK;
 }
@@ -881,7 +898,8 @@ static cosmica_status batch_items(const cosmica_batch *b, const cosmica_work_ite
         if (own && !valid_start(p, w.r0_AU, w.th0_rad, w.ph0_rad))
             return fail(COSMICA_ERR_INVALID, "item %u: start position outside the heliosphere", i);
         its[i] = make_item(w.T_GeVn, w.first_pid, w.seed, w.param_idx, w.species_idx, own ? w.r0_AU : p.r0_AU,
-                           own ? w.th0_rad : p.th0_rad, own ? w.ph0_rad : p.ph0_rad, i);
+                           own ? w.th0_rad : p.th0_rad, own ? w.ph0_rad : p.ph0_rad,
+                           w.exit_item_plus1 ? w.exit_item_plus1 - 1u : i);
         pre[i + 1] = pre[i] + w.n;
     }
     return COSMICA_OK;
@@ -993,6 +1011,30 @@ extern "C" cosmica_status cosmica_batch_spectrum(cosmica_batch *b, const cosmica
     }
     return run_spectrum(exit, its, lis, bins, J_out, sigma_out, hist_out, b->spec_items, b->spec_stage,
                         b->lis_buf, b->lis_stage, (cudaStream_t)stream);
+}
+
+extern "C" cosmica_status cosmica_batch_spectrum_hist(cosmica_batch *b, const cosmica_work_item *items,
+                                                      uint32_t n_items, const cosmica_lis *lis,
+                                                      const cosmica_bins *bins, const uint64_t *hist, double *J_out,
+                                                      double *sigma_out, void *stream)
+{
+    if (!b) return fail(COSMICA_ERR_INVALID, "batch is NULL");
+    if (n_items > 0 && !items) return fail(COSMICA_ERR_INVALID, "items is NULL");
+    double x_lo, dx;
+    cosmica_status st = check_bins(bins, &x_lo, &dx);
+    if (st != COSMICA_OK) return st;
+    if (n_items == 0) return COSMICA_OK;
+    if (!J_out || !sigma_out || !hist) return fail(COSMICA_ERR_INVALID, "J / sigma / hist must be non-NULL");
+    if (!is_device_ptr(J_out) || !is_device_ptr(sigma_out) || !is_device_ptr(hist))
+        return fail(COSMICA_ERR_INVALID, "J / sigma / hist must be device memory");
+    std::vector<SpecItem> its(n_items);
+    for (uint32_t i = 0; i < n_items; ++i) {
+        if (items[i].species_idx >= b->species.size()) return fail(COSMICA_ERR_INVALID, "species index out of range");
+        const cosmica_species &sp = b->species[items[i].species_idx];
+        its[i] = SpecItem{items[i].T_GeVn, (double)sp.A, (double)sp.Z, sp.m0_GeV};
+    }
+    return spectrum_of_hist(its, lis, bins->nbins, x_lo, dx, hist, J_out, sigma_out, b->spec_items, b->spec_stage,
+                            b->lis_buf, b->lis_stage, (cudaStream_t)stream);
 }
 
 // =============================================================== autotune ==
