@@ -3,7 +3,7 @@ device memory (a foreign memory pool holds the free memory, cudaFree's
 implicit device synchronisation is not allowed, or every allocation must go
 through an approved allocator).  Its scratch is a fixed static device array,
 so it must give exactly what cosmica_propagate gives for the same inputs, on
-consecutive calls that reuse the array.
+consecutive calls that reuse the array, up to its largest accepted size.
 
 This file is collected last so that a failure here leaves every other test
 already run; it also passes alone in a fresh process.
@@ -43,6 +43,9 @@ def test_noalloc_matches_propagate_on_consecutive_calls(precision):
     calls = [
         (W.params(max_steps=2_000_000), W.PROTON, [0.3, 3.0, 30.0], [37, 0, 90], 17),
         (W.config3_param_sets()[4] | {"max_steps": 2_000_000.0}, W.HELIUM4, [0.5, 5.0], [64, 33], 18),
+        # the largest accepted call: 1024 energies, which reach the scratch in many parameter chunks
+        (W.params(max_steps=2_000_000), W.ELECTRON, W.logspace(20.0, 100.0, 1024),
+         [(k % 3) for k in range(1024)], 19),
     ]
     for p, sp, T, n, seed in calls:          # two calls in a row share the static scratch
         params = cz.make_params(p, precision)
