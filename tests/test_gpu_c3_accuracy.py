@@ -1,0 +1,109 @@
+"""Accuracy of the mixed-precision path on the batched workload (64
+heliospheres x {p, He-4, e-} x 30 energies, tilts 5-75 deg, both polarity
+epochs, termination shock and heliopause), through the C ABI in the launch
+configuration bench.py times (autotuned shape, CUDA-graph replay).
+
+* Twelve items of the workload, spanning both epochs, tilts above 60 deg and
+  below 15 deg, the three species and 0.1-49 GeV/n, against the FP64 CPU
+  oracle's spectra for the very same quasi-particles (stored by
+  tests/golden/make_c3_golden.py): per item |dJ| <= 3 sigma (combined Monte
+  Carlo error) and |dJ| / J <= 0.5 %, for both accumulations of the mixed
+  step (compensated FP32 and FP64).
+* The compensated FP32 (float-float) accumulation against FP64 accumulation
+  path by path, on a model whose paths are not chaotic (unipolar field: no
+  current sheet, whose crossings amplify single roundings): both take the same
+  FP32 increments, so at least 99.9 % of the paths exit on the same step with
+  exit states within 1e-5 (relative for r and s, absolute for ln P, theta and
+  phi).  This is where compensated FP32
+  proves equivalent to FP64 accumulation on the batched workload's model.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2502_06319_gb300 import cosmica as cz
+from paper_2502_06319_gb300 import workloads as W
+from paper_2502_06319_gb300.sharding import items_of
+from tests.gpu_util import gpu_run, torch
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_c3_items.json")
+
+
+@pytest.fixture(scope="module")
+def golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("precision", [cz.PREC_MIXED, cz.PREC_MIXED_F64ACC], ids=["float-float", "f64acc"])
+def test_config3_items_match_the_oracle(golden, precision):
+    t = torch()
+    params, species, items = items_of(W.config3(), 0)
+    recs = golden["items"]
+    sel = []
+    for rec in recs:
+        it = items[rec["item"]]
+        assert (it[0], it[1], it[3], it[4], it[5]) == (rec["param_idx"], rec["species_idx"], rec["n"],
+                                                       rec["first_pid"], rec["seed"])
+        assert it[2] == rec["T"]
+        sel.append(it)
+    b = cz.cosmica_batch_create([cz.make_params(p, precision) for p in params],
+                                [cz.make_species(s) for s in species])
+    arr = cz.make_items(sel)
+    tune, _ = cz.cosmica_autotune(b, arr, len(sel))
+    tune.use_graph = 1
+    n = sum(i[3] for i in sel)
+    out = cz.ExitBuffers(n)
+    nb = golden["bins"][2]
+    J = t.empty(len(sel), dtype=t.float64, device="cuda")
+    S = t.empty_like(J)
+    H = t.empty(len(sel) * (nb + 3), dtype=t.int64, device="cuda")
+    s = t.cuda.Stream()
+    with t.cuda.stream(s):
+        for _ in range(2):      # the second run replays the captured graph
+            cz.cosmica_batch_run(b, arr, len(sel), out, tuning=tune, stream=s)
+        cz.cosmica_batch_spectrum(b, arr, len(sel), out, cz.make_bins(*golden["bins"][:2], nb), J, S, H, stream=s)
+    s.synchronize()
+    cz.cosmica_batch_destroy(b)
+    assert bool((out.status == cz.PATH_EXIT).all())
+    Jg, Sg = J.cpu().numpy(), S.cpu().numpy()
+    bad = []
+    for k, rec in enumerate(recs):
+        d = Jg[k] - rec["J"]
+        rel, z = d / rec["J"], abs(d) / math.hypot(Sg[k], rec["sigma"])
+        print(f"item {rec['item']:5d} set {rec['set']:2d} (tilt {rec['tilt_deg']:4.1f}, A {int(rec['polarity']):+d}) "
+              f"{rec['species']:8s} T {rec['T']:7.3f} n {rec['n']}: dJ/J {rel:+.5f} ({z:.2f} sigma, "
+              f"sigma_rel {rec['sigma'] / rec['J']:.4f})")
+        if not (abs(rel) <= 0.005 and z <= 3.0):
+            bad.append((rec["item"], rel, z))
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("polarity", [1.0, -1.0])
+def test_float_float_equals_fp64_accumulation_without_the_sheet(polarity):
+    p = W.params(hcs_on=0.0, polarity=polarity, tilt_deg=40.0, R_ts=85.0, ts_K_factor=0.5, R_out=122.0)
+    T = [0.2, 1.0, 5.0, 30.0]
+    for sp in (W.PROTON, W.HELIUM4, W.ELECTRON):
+        job = W.Job(p, sp, T, [1500] * len(T), seed=4242)
+        ff, _, m1 = gpu_run(job, precision=cz.PREC_MIXED)
+        f64, _, m2 = gpu_run(job, precision=cz.PREC_MIXED_F64ACC)
+        m1.close(); m2.close()
+        assert np.all(ff["status"] == cz.PATH_EXIT) and np.all(f64["status"] == cz.PATH_EXIT)
+        same = ff["steps"] == f64["steps"]
+        worst = {}
+        for k in ("r", "s"):
+            worst[k] = float(np.max(np.abs(ff[k][same] - f64[k][same]) / np.abs(f64[k][same])))
+        worst["lnP"] = float(np.max(np.abs(ff["lnP"][same] - f64["lnP"][same])))
+        dth = np.abs(ff["th"][same] - f64["th"][same])
+        dph = np.abs(ff["ph"][same] - f64["ph"][same])
+        worst["th"] = float(dth.max())
+        worst["ph"] = float(np.minimum(dph, 2 * np.pi - dph).max())
+        print(f"{sp} A {polarity:+.0f}: same exit step {same.mean():.5f}, worst differences {worst}")
+        assert same.mean() >= 0.999
+        assert worst["r"] <= 1e-5 and worst["lnP"] <= 1e-5 and worst["s"] <= 1e-5
+        assert worst["th"] <= 1e-5 and worst["ph"] <= 1e-5

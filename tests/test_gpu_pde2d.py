@@ -1,8 +1,11 @@
 """The CUDA path against the independent 2-D PDE solution of the axisymmetric
-model with drifts (unipolar field; flat current sheet; both polarity epochs),
-through the C ABI: mixed-precision spectra (Eq. 4, unbinned) within 3 sigma
-plus 0.5 % of the stored fine-grid solutions of the steady transport equation
-(Eq. 5), the same bar the FP64 oracle meets in test_oracle_pde2d.py.
+model with drifts (unipolar field: protons, He-4 and electrons; flat current
+sheet: protons; both polarity epochs each), through the C ABI: mixed-precision
+spectra (Eq. 4, unbinned) within 3 sigma plus 0.5 % of the stored fine-grid
+solutions of the steady transport equation (Eq. 5), the same bar the FP64
+oracle meets in test_oracle_pde2d.py.  He-4 (A/Z = 2) and electrons (negative
+charge, beta ~ 1) check the species-dependent parts of the mixed step: the
+rigidity of a kinetic energy per nucleon, beta, and the sign of the drift.
 """
 import json
 import math
@@ -25,15 +28,16 @@ def _golden():
         return json.load(f)
 
 
-@pytest.mark.parametrize("k", range(4))
+@pytest.mark.parametrize("k", range(8))
 @pytest.mark.parametrize("precision", [cz.PREC_MIXED, cz.PREC_MIXED_F64ACC], ids=["mixed", "f64acc"])
 def test_mixed_spectrum_matches_pde(k, precision):
     g = _golden()
-    case = [c for c in g["cases"] if c["species_name"] == "proton"][k]
+    case = g["cases"][k]
     job = W.Job(case["params"], case["species"], list(g["T0"]), [20000] * len(g["T0"]), seed=77)
     res, out, m = gpu_run(job, precision=precision)
     m.close()
     assert np.all(res["status"] == 1), np.bincount(res["status"])
     J, S = gpu_unbinned(job, out, 0)
     Jp = np.array(case["J"])
-    assert np.all(np.abs(J - Jp) < 3.0 * S + 0.005 * Jp), (case["name"], case["params"]["polarity"], J, Jp, S)
+    assert np.all(np.abs(J - Jp) < 3.0 * S + 0.005 * Jp), (case["name"], case["species_name"],
+                                                           case["params"]["polarity"], J, Jp, S)
