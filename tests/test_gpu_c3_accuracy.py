@@ -13,9 +13,9 @@ configuration bench.py times (autotuned shape, CUDA-graph replay).
   path by path, on a model whose paths are not chaotic (unipolar field: no
   current sheet, whose crossings amplify single roundings): both take the same
   FP32 increments, so at least 99.9 % of the paths exit on the same step with
-  exit states within 1e-5 (relative for r and s, absolute for ln P, theta and
-  phi).  This is where compensated FP32
-  proves equivalent to FP64 accumulation on the batched workload's model.
+  exit states within 1e-5 (relative for r, s and the exit point's Cartesian
+  position, absolute for ln P).  This is where compensated FP32 proves
+  equivalent to FP64 accumulation on the batched workload's model.
 """
 import json
 import math
@@ -84,6 +84,11 @@ def test_config3_items_match_the_oracle(golden, precision):
     assert not bad, bad
 
 
+def _xyz(o, m):
+    r, th, ph = o["r"][m], o["th"][m], o["ph"][m]
+    return np.array([r * np.sin(th) * np.cos(ph), r * np.sin(th) * np.sin(ph), r * np.cos(th)])
+
+
 @pytest.mark.parametrize("polarity", [1.0, -1.0])
 def test_float_float_equals_fp64_accumulation_without_the_sheet(polarity):
     p = W.params(hcs_on=0.0, polarity=polarity, tilt_deg=40.0, R_ts=85.0, ts_K_factor=0.5, R_out=122.0)
@@ -99,11 +104,9 @@ def test_float_float_equals_fp64_accumulation_without_the_sheet(polarity):
         for k in ("r", "s"):
             worst[k] = float(np.max(np.abs(ff[k][same] - f64[k][same]) / np.abs(f64[k][same])))
         worst["lnP"] = float(np.max(np.abs(ff["lnP"][same] - f64["lnP"][same])))
-        dth = np.abs(ff["th"][same] - f64["th"][same])
-        dph = np.abs(ff["ph"][same] - f64["ph"][same])
-        worst["th"] = float(dth.max())
-        worst["ph"] = float(np.minimum(dph, 2 * np.pi - dph).max())
+        # the exit point as a Cartesian position: near a pole the longitude is ill-conditioned
+        # (one FP32 ulp of sin(theta) changes a phi increment of ~1e4 rad by 2^-10), the point is not
+        worst["x"] = float(np.max(np.linalg.norm(_xyz(ff, same) - _xyz(f64, same), axis=0) / f64["r"][same]))
         print(f"{sp} A {polarity:+.0f}: same exit step {same.mean():.5f}, worst differences {worst}")
         assert same.mean() >= 0.999
-        assert worst["r"] <= 1e-5 and worst["lnP"] <= 1e-5 and worst["s"] <= 1e-5
-        assert worst["th"] <= 1e-5 and worst["ph"] <= 1e-5
+        assert worst["r"] <= 1e-5 and worst["lnP"] <= 1e-5 and worst["s"] <= 1e-5 and worst["x"] <= 1e-5
