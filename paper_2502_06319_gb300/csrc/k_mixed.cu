@@ -83,12 +83,11 @@ __device__ __forceinline__ bool step(const LaunchArgs &a, Lane &L, Acc<ACC> &x, 
     x.boundaries(P32F(q, r_in));
     L.k += 1u;
 
-    int status = COSMICA_PATH_RUNNING;
-    if (!x.finite()) status = COSMICA_PATH_NONFINITE;
-    else if ((EXT && P32F(q, sq) != 0.0f) ? m32::outside_squashed(q, x.fr(), x.fth(), x.fph()) : x.exited())
-        status = COSMICA_PATH_EXIT;
-    else if (L.k >= L.max_steps) status = COSMICA_PATH_STEP_LIMIT;
-    if (status == COSMICA_PATH_RUNNING) return false;
+    const bool fin = x.finite();
+    const bool out = (EXT && P32F(q, sq) != 0.0f) ? m32::outside_squashed(q, x.fr(), x.fth(), x.fph()) : x.exited();
+    const bool lim = L.k >= L.max_steps;
+    if (fin & !out & !lim) return false;     // one rarely taken branch for the three ends of a path
+    const int status = !fin ? COSMICA_PATH_NONFINITE : (out ? COSMICA_PATH_EXIT : COSMICA_PATH_STEP_LIMIT);
     x.write(a.out, L.g);
     if constexpr (EN) {
         const double T = en.T64();
@@ -128,7 +127,10 @@ __global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a, uint32_t 
     uint32_t tick = 0;   // phase 1: steps since the last drained check; phase 2: steps since the checkpoint
 
     while (true) {
-        if (!phase2) {
+        if (!COMPACT && drained) {
+            // the queue is exhausted (warp-uniform): finish the particles in hand
+            if (!__any_sync(0xffffffffu, active)) break;
+        } else if (!phase2) {
             const unsigned need = __ballot_sync(0xffffffffu, !active && !drained);
             if (need) {
                 unsigned long long base = 0;
@@ -144,6 +146,9 @@ __global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a, uint32_t 
                         drained = true;
                     }
                 }
+                // without compaction a lane that was refused never asks again, so once any lane
+                // of the warp is refused the whole warp can stop asking
+                if (!COMPACT && base + __popc(need) > a.n_total) drained = true;
             }
             if (COMPACT) {
                 // learn of the drained queue even when no lane of the warp needed work
@@ -158,8 +163,6 @@ __global__ void __launch_bounds__(256) k_propagate_mixed(LaunchArgs a, uint32_t 
                     phase2 = true;
                     tick = 0;
                 }
-            } else if (!__any_sync(0xffffffffu, active)) {
-                break;
             }
         }
         if (COMPACT && phase2) {

@@ -155,12 +155,12 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
         S.L.k += 1u;
         used += 1u;
 
-        int status = COSMICA_PATH_RUNNING;
-        if (!x.finite()) status = COSMICA_PATH_NONFINITE;
-        else if ((EXT && P32F(q, sq) != 0.0f) ? m32::outside_squashed(q, x.fr(), x.fth(), x.fph()) : x.exited())
-            status = COSMICA_PATH_EXIT;
-        else if (S.L.k >= S.L.max_steps) status = COSMICA_PATH_STEP_LIMIT;
-        if (status != COSMICA_PATH_RUNNING) {
+        const bool fin = x.finite();
+        const bool out = (EXT && P32F(q, sq) != 0.0f) ? m32::outside_squashed(q, x.fr(), x.fth(), x.fph())
+                                                       : x.exited();
+        const bool lim = S.L.k >= S.L.max_steps;
+        if (!(fin & !out & !lim)) {      // one rarely taken branch for the three ends of a path
+            const int status = !fin ? COSMICA_PATH_NONFINITE : (out ? COSMICA_PATH_EXIT : COSMICA_PATH_STEP_LIMIT);
             const uint64_t g = S.exit_idx;
             x.write(a.arena, g);
             a.arena.steps[g] = S.L.k;

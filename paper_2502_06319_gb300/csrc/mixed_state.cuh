@@ -59,12 +59,16 @@ struct Acc<COSMICA_PREC_MIXED> {
     // reflect at r_in, fold theta at the poles, wrap phi; all rare branches
     __device__ void boundaries(float r_in)
     {
-        if (r.hi < r_in) {           // r <- 2 r_in - r
-            r.hi = -r.hi; r.lo = -r.lo;
-            m32::ff_add(r, r_in2);
+        const bool fold = th.hi < 0.0f || pole_distance() < 0.0f;   // theta < 0 or theta > pi
+        // one rarely taken branch for the three boundaries
+        if ((r.hi < r_in) | fold | (ph.hi < 0.0f) | (ph.hi >= m32::kTwoPiF)) {
+            if (r.hi < r_in) {           // r <- 2 r_in - r
+                r.hi = -r.hi; r.lo = -r.lo;
+                m32::ff_add(r, r_in2);
+            }
+            if (fold) fold_theta();
+            if (ph.hi < 0.0f || ph.hi >= m32::kTwoPiF) wrap_phi();
         }
-        if (th.hi < 0.0f || pole_distance() < 0.0f) fold_theta();    // theta < 0 or theta > pi
-        if (ph.hi < 0.0f || ph.hi >= m32::kTwoPiF) wrap_phi();
     }
     __device__ void fold_theta()
     {
