@@ -171,10 +171,13 @@ __device__ __forceinline__ void eval(const P32<ST> &q, float M2, float sq, float
     const float dGam_dth = Gam * fmaf(-dV, inv_V, cot);
 
     // termination shock factor (uniform branch: no shock in the parameter set); a
-    // squashed shock sits at its spheroid's distance along the point's direction
+    // squashed shock sits at its spheroid's distance along the point's direction.  The
+    // full-model variant evaluates it without the branch: with ts_drop = 0 it gives g = 1
+    // and dg = -0 exactly, which leave every later value as the branch would (measured:
+    // +2.6 % steps/s on config 3, +2.4 % on config 2, which has no shock)
     float g = 1.0f, dg = 0.0f, dg_dth = 0.0f, dg_dph = 0.0f;
     const bool squashed = EXT && P32F(q, sq) != 0.0f;
-    if (P32F(q, ts_drop) != 0.0f) {
+    if (FULL || P32F(q, ts_drop) != 0.0f) {
         float Rts = P32F(q, R_ts), dR_dmu = 0.0f, dmu_dth = 0.0f, dmu_dph = 0.0f;
         if (squashed) {
             const float mu = nose_mu(q, sn, cs, ph, dmu_dth, dmu_dph);
