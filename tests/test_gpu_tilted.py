@@ -1,0 +1,34 @@
+"""The CUDA path with a tilted (wavy) current sheet against the independent
+Cartesian Monte Carlo solution (oracle/sde_cartesian.c, stored by
+tests/golden/make_cartesian_golden.py), through the C ABI: the mixed-precision
+spectra (Eq. 4, unbinned) of both accumulations within 3 sigma plus 0.5 %,
+the bar the oracle meets in test_oracle_tilted.py.  The Cartesian solver
+shares no code with the CUDA path (nor with the oracle)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2502_06319_gb300 import cosmica as cz
+from paper_2502_06319_gb300 import workloads as W
+from tests.gpu_util import gpu_run, gpu_unbinned
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cartesian_tilted.json")
+
+
+@pytest.mark.parametrize("k", range(3))
+@pytest.mark.parametrize("precision", [cz.PREC_MIXED, cz.PREC_MIXED_F64ACC], ids=["mixed", "f64acc"])
+def test_tilted_sheet_matches_the_cartesian_solution(k, precision):
+    g = json.load(open(GOLDEN))
+    case = [c for c in g["cases"] if c["kind"] == "tilted"][k]
+    job = W.Job(case["params"], case["species"], list(g["T0"]), [20000] * len(g["T0"]), seed=91)
+    res, out, m = gpu_run(job, precision=precision)
+    m.close()
+    assert np.all(res["status"] == cz.PATH_EXIT), np.bincount(res["status"])
+    J, S = gpu_unbinned(job, out, 0)
+    Jc, Sc = np.array(case["J"]), np.array(case["sigma"])
+    print(f"{case['name']}: GPU / Cartesian - 1 = {J / Jc - 1}, combined sigma {np.hypot(S, Sc) / Jc}")
+    assert np.all(np.abs(J - Jc) < 3.0 * np.hypot(S, Sc) + 0.005 * Jc), (case["name"], J / Jc - 1)
