@@ -441,10 +441,10 @@ cosmica_status cosmica_batch_spectrum_hist(cosmica_batch *batch, const cosmica_w
 
 /* Pick a launch shape for this batch by timing candidate shapes (block size,
  * resident blocks, compaction period) and write the fastest to *best (its
- * predicted steps/s in *best_rate if not NULL).  Batches of up to ~6 particles
- * per resident lane are timed whole; larger ones on two scaled samples of
- * `items` (host), from which each candidate's time for the whole batch is
- * extrapolated linearly in the particle count.  Results are cached for the
+ * predicted steps/s in *best_rate if not NULL).  Batches of up to ~30 particles
+ * per SM thread slot are timed whole; larger ones on two scaled samples of
+ * `items` (host; ~10 and ~30 particles per slot), from which each candidate's
+ * time for the whole batch is extrapolated linearly in the particle count.  Results are cached for the
  * process per device and configuration class (precision, drift, termination
  * shock, particle count within a factor of two, kernel variant); a cached
  * class returns at once.  Synchronous; uses the batch's own scratch.  An FP64

@@ -1086,14 +1086,15 @@ extern "C" cosmica_status cosmica_autotune(cosmica_batch *b, const cosmica_work_
     if (pre[n_items] == 0) return fail(COSMICA_ERR_INVALID, "autotune needs particles");
     // A launch's time is about t(P) = a + b P in its particle count P: b is the cost of a
     // particle at full occupancy, a the tail that no launch avoids (its slowest paths run
-    // alone at the end).  Small batches (up to ~6 particles per resident lane) are timed
-    // whole; larger ones on two scaled samples (~2 and ~6 per lane), from which each
-    // candidate's time for the whole batch is extrapolated.  A single small sample would
-    // over-weight the tail and favour shapes that are slower on the full batch.
+    // alone at the end).  Small batches (up to ~30 particles per SM thread slot) are timed
+    // whole; larger ones on two scaled samples (~10 and ~30 per slot), from which each
+    // candidate's time for the whole batch is extrapolated.  Small samples over-weight the
+    // tail and favour shapes with fewer resident warps: with samples of ~2 and ~6 per slot
+    // the tuner chose 3 blocks of 256 on config 3, which runs 2.6 % slower than 4.
     const uint64_t lanes = (uint64_t)num_sms() * 2048u;
     const uint64_t n_full = pre[n_items];
-    const double s_hi = std::min(1.0, 6.0 * (double)lanes / (double)n_full);
-    const double s_lo = std::min(1.0, 2.0 * (double)lanes / (double)n_full);
+    const double s_hi = std::min(1.0, 30.0 * (double)lanes / (double)n_full);
+    const double s_lo = std::min(1.0, 10.0 * (double)lanes / (double)n_full);
     const bool whole = s_hi >= 1.0;
     auto make_sample = [&](double scale, uint64_t *total) {
         std::vector<cosmica_work_item> v(items, items + n_items);
