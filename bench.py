@@ -69,8 +69,8 @@ SM_LANES_PER_CLK = 128      # 4 SMSPs x 32 lanes: one warp instruction per SMSP 
 # reduced count; the bytes are the work-item reads and exit-record writes, so they scale
 # with the particles of a launch (commands in profiles/).  They describe the kernel built
 # from the sources whose SHA-256 is recorded; any other build reports traffic null.
-TRAFFIC = {"c3": {"bytes_per_particle": 220248064 / 3715361,   # 43 469 568 read + 176 778 496 written, 5 % scale
-                  "sources_sha256": "d17125f5b0346e43e468c15dcd5cae77ed29804ebf13fcc4d35217a3e67b63ae"}}
+TRAFFIC = {"c3": {"bytes_per_particle": 257347072 / 3715361,   # 57 048 064 read + 200 299 008 written, 5 % scale
+                  "sources_sha256": "0d7d8d1018f6be1449eebf55aee1e53dcea69fce6e02098f038d1653968b5cda"}}
 KERNEL_SOURCES = ("common.cuh", "philox.cuh", "model32.cuh", "mixed_state.cuh", "k_mixed.cu")
 
 
