@@ -71,8 +71,9 @@ struct ServeArgs {
     uint32_t budget;               // steps per lane per quantum
 };
 
-cudaError_t launch_serve(const ServeArgs &a, int acc, bool ext, PersistentShape shape, cudaStream_t s);
-int serve_max_blocks_per_sm(int acc, bool ext, unsigned block);
+// full: every resident request is the full model (the variant without uniform branches)
+cudaError_t launch_serve(const ServeArgs &a, int acc, bool ext, bool full, PersistentShape shape, cudaStream_t s);
+int serve_max_blocks_per_sm(int acc, bool ext, bool full, unsigned block);
 
 void note_launch();
 

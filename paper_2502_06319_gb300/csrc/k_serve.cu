@@ -18,6 +18,7 @@
 // parameters), and suspension stores its state exactly, so every result is
 // the same alone and in any mix.
 #include <cstdint>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -65,8 +66,11 @@ struct ServeLane {
 };
 
 // EXT: some resident request has radial shells or a squashed heliosphere (the
-// extended model; compile-time, as in the batched kernel).
-template <int ACC, bool EXT>
+// extended model; compile-time, as in the batched kernel).  FULL: every resident
+// request is the full model (drift and current sheet on, adaptive step), so the step
+// carries no uniform branch on those switches (the same DAG as the batched kernel's
+// full-model variant).
+template <int ACC, bool EXT, bool FULL>
 __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
 {
     const unsigned lane = threadIdx.x & 31u;
@@ -74,6 +78,7 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
     Acc<ACC> x;
     bool active = false, done = false;
     uint32_t used = 0;
+    float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f;   // normals of the lane's next step (drawn one step ahead)
 
     while (true) {
         unsigned need = __ballot_sync(0xffffffffu, !active && !done);
@@ -101,6 +106,7 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
                     S.slot = rec.slot;
                     S.energy = rec.energy;
                     S.exit_idx = rec.exit_idx;
+                    m32::normals(S.L.seed, S.L.pid, S.L.k, z0, z1, z2);
                     active = got = true;
                 }
             }
@@ -131,6 +137,7 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
                         const double T = item.T;
                         const double P0 = sp.A / fabs(sp.Z) * sqrt(T * (T + 2.0 * sp.m0));
                         x.init(p.r0, p.th0, p.ph0, log(P0), p.R_out, p.f.r_in);
+                        m32::normals(S.L.seed, S.L.pid, S.L.k, z0, z1, z2);
                         active = true;
                     } else {
                         done = true;
@@ -141,11 +148,9 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
         if (!__any_sync(0xffffffffu, active)) break;
         if (!active) continue;
 
-        float z0, z1, z2;
-        m32::normals(S.L.seed, S.L.pid, S.L.k, z0, z1, z2);
         m32::Drift c;
         const P32<1> q{S.L.q};
-        m32::eval<EXT, false, 1>(q, S.L.M2, S.L.sq, x.fr(), x.fth(), x.sin_th(), x.fph(), x.flnP(), c);
+        m32::eval<EXT, FULL, 1>(q, S.L.M2, S.L.sq, x.fr(), x.fth(), x.sin_th(), x.fph(), x.flnP(), c);
         const float sdt = sqrtf(c.dt);
         const float dr = fmaf(c.Ar_tot, c.dt, c.l00 * z0 * sdt);
         const float dth = fmaf(c.dth_drift, c.dt, c.l11 * z1 * sdt * c.inv_r);
@@ -183,6 +188,10 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
             a.suspend[j] = rec;     // j < grid x block: each lane suspends at most once
             active = false;
             done = true;
+        } else {
+            // the next step's normals, drawn after this step's arithmetic (as in the batched
+            // kernel: the Philox block and the coefficient evaluation are never live together)
+            m32::normals(S.L.seed, S.L.pid, S.L.k, z0, z1, z2);
         }
         if (used >= a.budget) done = true;
     }
@@ -190,30 +199,39 @@ __global__ void __launch_bounds__(256) k_serve(ServeArgs a)
 
 }  // namespace
 
-int serve_max_blocks_per_sm(int acc, bool ext, unsigned block)
+// Call fn(acc, extended, full) with each flag as a compile-time constant.
+template <class Fn>
+static void visit_serve(int acc, bool ext, bool full, Fn &&fn)
+{
+    auto on_acc = [&](auto A) {
+        auto on_ext = [&](auto X) {
+            if (full) fn(A, X, std::true_type{});
+            else fn(A, X, std::false_type{});
+        };
+        if (ext) on_ext(std::true_type{});
+        else on_ext(std::false_type{});
+    };
+    if (acc == COSMICA_PREC_MIXED_F64ACC) on_acc(std::integral_constant<int, COSMICA_PREC_MIXED_F64ACC>{});
+    else on_acc(std::integral_constant<int, COSMICA_PREC_MIXED>{});
+}
+
+int serve_max_blocks_per_sm(int acc, bool ext, bool full, unsigned block)
 {
     int nb = 0;
-    if (acc == COSMICA_PREC_MIXED_F64ACC)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ext ? k_serve<COSMICA_PREC_MIXED_F64ACC, true>
-                                                               : k_serve<COSMICA_PREC_MIXED_F64ACC, false>,
+    visit_serve(acc, ext, full, [&](auto A, auto X, auto F) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_serve<decltype(A)::value, decltype(X)::value,
+                                                                    decltype(F)::value>,
                                                       (int)block, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ext ? k_serve<COSMICA_PREC_MIXED, true>
-                                                               : k_serve<COSMICA_PREC_MIXED, false>,
-                                                      (int)block, 0);
+    });
     return nb;
 }
 
-cudaError_t launch_serve(const ServeArgs &a, int acc, bool ext, PersistentShape shape, cudaStream_t s)
+cudaError_t launch_serve(const ServeArgs &a, int acc, bool ext, bool full, PersistentShape shape, cudaStream_t s)
 {
     cudaGetLastError();
-    if (acc == COSMICA_PREC_MIXED_F64ACC) {
-        if (ext) k_serve<COSMICA_PREC_MIXED_F64ACC, true><<<shape.grid, shape.block, 0, s>>>(a);
-        else k_serve<COSMICA_PREC_MIXED_F64ACC, false><<<shape.grid, shape.block, 0, s>>>(a);
-    } else {
-        if (ext) k_serve<COSMICA_PREC_MIXED, true><<<shape.grid, shape.block, 0, s>>>(a);
-        else k_serve<COSMICA_PREC_MIXED, false><<<shape.grid, shape.block, 0, s>>>(a);
-    }
+    visit_serve(acc, ext, full, [&](auto A, auto X, auto F) {
+        k_serve<decltype(A)::value, decltype(X)::value, decltype(F)::value><<<shape.grid, shape.block, 0, s>>>(a);
+    });
     note_launch();
     return cudaGetLastError();
 }

@@ -228,12 +228,14 @@ bool cosmica_server::quantum(std::vector<uint64_t> &admitted_now)
     std::vector<uint64_t> pre(1, 0);
     std::vector<std::pair<uint64_t, uint32_t>> owner;   // (ticket, energy) per item
     bool ext = false;   // a resident request has radial shells or a squashed heliosphere
+    bool full = true;   // every resident request is the full model
     {
         std::lock_guard<std::mutex> lk(mu);
         for (auto &kv : reqs) {
             Req &r = kv.second;
             if (r.state != 1) continue;
             ext = ext || r.p.n_shells > 0 || r.p.squashed != 0;
+            full = full && full_model(r.p);
             for (uint32_t e = 0; e < r.T.size(); ++e) {
                 const uint64_t left = r.n[e] - r.started[e];
                 if (!left) continue;
@@ -278,7 +280,7 @@ bool cosmica_server::quantum(std::vector<uint64_t> &admitted_now)
     a.budget = budget;
     cudaError_t e = cudaMemsetAsync(d_cursors, 0, 2 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_nsusp, 0, sizeof(unsigned int), stream);
-    if (e == cudaSuccess) e = launch_serve(a, precision, ext, shape, stream);
+    if (e == cudaSuccess) e = launch_serve(a, precision, ext, full, shape, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_cursor, d_cursors, sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_nsusp, d_nsusp, sizeof(unsigned int), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_done, d_done, kMaxSlots * sizeof(unsigned int), cudaMemcpyDeviceToHost, stream);
@@ -374,9 +376,10 @@ extern "C" cosmica_status cosmica_server_create(size_t mem_budget, int32_t preci
     s->t0 = std::chrono::steady_clock::now();
     cudaGetDevice(&s->device);
     const unsigned block = 128;
-    // sized for the basic model's kernel; the extended variant's extra blocks (if it has
-    // fewer resident) start as others finish and take whatever work is left
-    const int bps = std::max(1, serve_max_blocks_per_sm(precision, false, block));
+    // sized for the full model's kernel (the common case); a variant with fewer resident
+    // blocks (extended heliosphere, or a model without drift or sheet) starts its extra
+    // blocks as others finish, and they take whatever work is left
+    const int bps = std::max(1, serve_max_blocks_per_sm(precision, false, true, block));
     s->shape = PersistentShape{block, (unsigned)(num_sms() * bps), 0u};
     s->lane_cap = (uint64_t)s->shape.grid * block;
     const size_t fixed = 2 * s->lane_cap * sizeof(Suspended) + kMaxSlots * (sizeof(DevParams) + sizeof(DevSpecies) + 12) +
