@@ -55,6 +55,8 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert L.cosmica_propagate(None, None, None, 0, None, 1, None, None) == cz.ERR_INVALID
     assert L.cosmica_batch_create(None, 0, None, 0, C.byref(h)) == cz.ERR_INVALID
     assert L.cosmica_batch_run(None, None, 0, None, None, None, None) == cz.ERR_INVALID
+    assert L.cosmica_batch_spectrum_hist(None, None, 0, None, None, None, None, None, None) == cz.ERR_INVALID
+    assert b"batch is NULL" in L.cosmica_last_error()
     assert L.cosmica_debug_fn64(9, 0, None, None, None) == cz.ERR_INVALID
 
 
