@@ -8,8 +8,15 @@ checked instead:
   * sampled items, re-run alone, give bit-identical exit records (a path
     depends only on its seed, identity, parameters, species and energy);
   * the spectrum of the smallest item of each species agrees with the FP64
-    oracle's within 3 sigma (the oracle runs the same particles).
+    oracle's within 3 sigma (the oracle runs the same particles);
+  * the twelve items of the stored oracle result (tests/golden/oracle_c3_items.json:
+    both polarity epochs, tilts 73/64/11/8 deg, p/He-4/e-, 4-5e4 paths each), taken
+    from this full-size launch, agree with it within 3 sigma and 0.5 %.
 """
+import json
+import math
+import os
+
 import numpy as np
 import pytest
 
@@ -83,4 +90,13 @@ def test_config3_full_size_properties(orc):
         print(f"full-size item {k} ({species[si]}, T {T_:.3g}, n {n}): mixed/oracle - 1 = {Jn[k] / Jo[0] - 1:.4f}, "
               f"sigma_rel {So[0] / Jo[0]:.4f}")
         assert abs(Jn[k] - Jo[0]) <= 3 * np.hypot(Sn[k], So[0]), (k, Jn[k], Jo[0], Sn[k], So[0])
+
+    # the stored oracle items, from the full-size launch
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_c3_items.json")) as f:
+        golden = json.load(f)
+    for rec in golden["items"]:
+        k = rec["item"]
+        assert (items[k][3], items[k][4]) == (rec["n"], rec["first_pid"])
+        d = Jn[k] - rec["J"]
+        assert abs(d) <= 3.0 * math.hypot(Sn[k], rec["sigma"]) and abs(d) <= 0.005 * rec["J"], (k, d / rec["J"])
     cz.cosmica_batch_destroy(b)
