@@ -22,7 +22,9 @@ throughput the line carries:
   * serving: the continuous-batching server under Poisson request streams at
     0.5x and 0.8x of its measured capacity (p50/p99 latency, spectra/s);
   * cpu_baseline: the FP64 oracle on the host cores (all cores and one core)
-    on stratified samples.
+    on stratified samples;
+  * config2: config 2 (one heliosphere, 30 energies x 20 000 protons) timed
+    beside it, a workload bound by its slowest paths rather than by issue.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 launch with torch.distributed.run.  Default (--scaling strong): one
@@ -113,6 +115,8 @@ def parse():
     ap.add_argument("--fp64-sample", type=int, default=46080,
                     help="quasi-particles of the stratified sample the plain FP64 path is timed on (0: skip)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--no-c2", action="store_true",
+                    help="skip the config-2 key of the default line (30 energies x 20 000 protons, tail-bound)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="quasi-particles of the oracle's stratified sample (all cores; reference arm: per step)")
@@ -579,6 +583,45 @@ def main():
                 "accuracy": "FP64 GPU paths are bit-identical to the FP64 oracle (tests); the mixed spectra's error "
                             "against the oracle is spectrum_error"}
 
+    # config 2 beside the headline: one heliosphere, 6e5 paths, bound by its slowest paths
+    config2 = None
+    if args.workload == "c3" and not args.no_c2 and world == 1 and prec == cz.PREC_MIXED:
+        j2 = W.config2()
+        p2, s2, it2 = items_of([j2], 0)
+        b2 = cz.cosmica_batch_create([cz.make_params(p, prec) for p in p2], [cz.make_species(x) for x in s2])
+        a2 = cz.make_items(it2)
+        t2, _ = cz.cosmica_autotune(b2, a2, len(it2))
+        t2.use_graph = 1
+        o2 = cz.ExitBuffers(sum(i[3] for i in it2))
+        J2 = torch.empty(len(it2), dtype=torch.float64, device="cuda")
+        S2 = torch.empty_like(J2)
+        H2 = torch.empty(len(it2) * (j2.bins.n + 3), dtype=torch.int64, device="cuda")
+        bins2 = cz.make_bins(j2.bins.P_min, j2.bins.P_max, j2.bins.n)
+        ms2, st2 = 0.0, 0
+        for rep in range(5):          # 2 warm-up + 3 timed passes
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                cz.cosmica_batch_run(b2, a2, len(it2), o2, tuning=t2, steps_out=steps_dev, stream=stream)
+                cz.cosmica_batch_spectrum(b2, a2, len(it2), o2, bins2, J2, S2, H2, stream=stream)
+                e1.record(stream)
+            e1.synchronize()
+            if rep >= 2:
+                ms2 += e0.elapsed_time(e1)
+                st2 += int(steps_dev.item())
+        cz.cosmica_batch_destroy(b2)
+        rate2 = st2 / (ms2 * 1e-3)
+        config2 = {"workload": "config2: full model, proton, 30 energies x 20000 (one heliosphere, 6e5 paths)",
+                   "steps_per_s": rate2, "ms_per_pass": ms2 / 3, "spectra_per_s": 3 / (ms2 * 1e-3),
+                   "issue_roofline_frac": sum(ALG_INST_PER_STEP.values()) * rate2 / 1e12 / (
+                       SM_LANES_PER_CLK * torch.cuda.get_device_properties(local).multi_processor_count
+                       * (clk.get("sm_mhz") or 2070.0) * 1e6 / 1e12),
+                   "tuning": {"block": t2.block, "blocks_per_sm": t2.blocks_per_sm,
+                              "compact_period": t2.compact_period},
+                   "note": "bound by its slowest paths (a lone path's step), not by issue"}
+
     serving = None
     if args.serve_requests > 0 and world == 1 and prec != cz.PREC_FP64:
         serving = serve_bench(cz, prec, n_cap=max(8, args.serve_requests // 4), n_load=args.serve_requests)
@@ -625,7 +668,7 @@ def main():
             "e2e": {"value": e2e_steps / e2e_s if e2e_s else None, "unit": "steps/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "passes": max(1, args.e2e_steps)},
             "gpu_launches": launches, "clocks": clk, "roofline": roof, "spectrum_error": err,
-            "fp64_plain": fp64, "serving": serving}
+            "fp64_plain": fp64, "serving": serving, "config2": config2}
     if rank == 0 and not args.no_cpu and world == 1:
         n_all = default_cpu_sample(args, len(items_spec), reference=False)
         cb = cpu_baseline(params, species, items_spec, n_all)
