@@ -35,9 +35,14 @@
  * Cartesian finite differences (Ito drift, curl, divergence), the closed-form
  * gradient-curvature drift and invariants; whole paths of the anisotropic
  * model with drifts, with no current sheet or a flat one (axisymmetric), are
- * pinned by an independent 2-D PDE solver.  Whole-path results of the full
- * model with the wavy (tilted) current sheet are "parity unpinned" beyond
- * those pins: no independent solution exists.
+ * pinned by an independent 2-D PDE solver; with the wavy (tilted) current
+ * sheet, where no 2-D reduction exists, by an independent Monte Carlo solver
+ * stepped in Cartesian coordinates (sde_cartesian.c: finite-difference
+ * divergence of K and curl of the drift potential, its own noise factor and
+ * random numbers), itself pinned to the 2-D PDE on the axisymmetric cases.
+ * The adaptive step rule is pinned by scaling every limit of the rule: the
+ * spectrum's deviation from the PDE falls as the square root of the step, and
+ * the Richardson extrapolation to dt -> 0 meets the PDE.
  */
 #include <math.h>
 #include <stdint.h>
