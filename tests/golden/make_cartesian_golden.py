@@ -14,10 +14,14 @@ that the paths are short enough for many samples):
     sheet, both polarity epochs), whose exact solutions the 2-D PDE gives --
     they pin this solver itself;
   * "tilted": the wavy current sheet (Sec. II.B), which no 2-D reduction
-    covers: tilt 30 deg with the standard rotation in both epochs, and tilt 60
-    deg with a 100-day rotation (a slower spiral, where the longitude equation
-    weighs more) in the A < 0 epoch, in which the sheet's drift carries the
-    particles.
+    covers: protons with a tilt of 30 deg and the standard rotation in both
+    epochs, and with a tilt of 60 deg and a 100-day rotation (a slower spiral,
+    where the longitude equation weighs more) in the A < 0 epoch, in which the
+    sheet's drift carries positive particles; electrons (negative charge,
+    beta ~ 1) with a tilt of 30 deg in the A > 0 epoch, in which it carries
+    negative ones; He-4 (A/Z = 2) with a tilt of 30 deg in the A < 0 epoch.
+Cases already in the output file are kept (the file is rewritten after every
+case, so an interrupted run resumes where it stopped).
 Every limit of the step rule is divided by 4 (step_scale 0.25), halving the
 O(sqrt(dt)) bias of testing for the exit after each step.
 """
@@ -33,15 +37,20 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 from oracle import cartesian as CC  # noqa: E402
+from paper_2502_06319_gb300 import workloads as W  # noqa: E402
 
 STEP_SCALE = 0.25
 SEED = 3
 
 
 def tilted_cases(base):
-    return [("tilt30_A+", dict(base, hcs_on=1.0, tilt_deg=30.0, polarity=1.0)),
-            ("tilt30_A-", dict(base, hcs_on=1.0, tilt_deg=30.0, polarity=-1.0)),
-            ("tilt60_rot100_A-", dict(base, hcs_on=1.0, tilt_deg=60.0, polarity=-1.0, rot_period_day=100.0))]
+    """(name, parameters, species) of the tilted-sheet cases."""
+    P, E, H = W.PROTON, W.ELECTRON, W.HELIUM4
+    return [("tilt30_A+", dict(base, hcs_on=1.0, tilt_deg=30.0, polarity=1.0), P),
+            ("tilt30_A-", dict(base, hcs_on=1.0, tilt_deg=30.0, polarity=-1.0), P),
+            ("tilt60_rot100_A-", dict(base, hcs_on=1.0, tilt_deg=60.0, polarity=-1.0, rot_period_day=100.0), P),
+            ("tilt30_electron_A+", dict(base, hcs_on=1.0, tilt_deg=30.0, polarity=1.0), E),
+            ("tilt30_he4_A-", dict(base, hcs_on=1.0, tilt_deg=30.0, polarity=-1.0), H)]
 
 
 def main():
@@ -51,9 +60,17 @@ def main():
     protons = [c for c in g["cases"] if c["species_name"] == "proton"]
     jobs = [("validation", f"{c['name']}_A{'+' if c['params']['polarity'] > 0 else '-'}", c["params"],
              c["species"], 8000) for c in protons]
-    jobs += [("tilted", name, p, protons[0]["species"], 20000) for name, p in tilted_cases(protons[0]["params"])]
+    jobs += [("tilted", name, p, sp, 20000) for name, p, sp in tilted_cases(protons[0]["params"])]
+    path = os.path.join(ROOT, "tests", "golden", "cartesian_tilted.json")
     out = {"T0": T0, "step_scale": STEP_SCALE, "seed": SEED, "cases": []}
+    if os.path.exists(path):
+        old = json.load(open(path))
+        if (old["T0"], old["step_scale"], old["seed"]) == (T0, STEP_SCALE, SEED):
+            out = old
+    done = {c["name"] for c in out["cases"]}
     for kind, name, p, sp, n in jobs:
+        if name in done:
+            continue
         t0 = time.time()
         res = CC.run(p, sp, T0, [n] * len(T0), seed=SEED, step_scale=STEP_SCALE)
         J, S = CC.spectrum(res, sp, T0)
@@ -62,7 +79,7 @@ def main():
                "status_counts": np.bincount(res["status"], minlength=4).tolist(), "seconds": time.time() - t0}
         out["cases"].append(rec)
         print(kind, name, "J", J, "sigma_rel", S / J, "steps", rec["mean_steps"], "s", round(rec["seconds"]), flush=True)
-        with open(os.path.join(ROOT, "tests", "golden", "cartesian_tilted.json"), "w") as f:
+        with open(path, "w") as f:
             json.dump(out, f)
 
 

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cartesian_tilted.json")
 
 
-@pytest.mark.parametrize("k", range(3))
+@pytest.mark.parametrize("k", range(5))
 @pytest.mark.parametrize("precision", [cz.PREC_MIXED, cz.PREC_MIXED_F64ACC], ids=["mixed", "f64acc"])
 def test_tilted_sheet_matches_the_cartesian_solution(k, precision):
     g = json.load(open(GOLDEN))

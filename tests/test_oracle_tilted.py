@@ -11,9 +11,10 @@ factor or the coordinate scalings of the longitude equation with the oracle.
 Its stored solutions (tests/golden/make_cartesian_golden.py) are first pinned
 to the independent 2-D PDE solutions where those exist (unipolar field and
 flat sheet, both epochs); the oracle must then agree with the tilted-sheet
-solutions within 3 sigma plus 0.5 % (the allowance of the 2-D PDE pin, for the
-bias of testing for the exit after each step), and the tilt must matter far
-beyond that allowance.
+solutions -- protons in both epochs and with a slower spiral, electrons in the
+epoch whose sheet drift carries negative charges, He-4 (A/Z = 2) -- within 3
+sigma plus 0.5 % (the allowance of the 2-D PDE pin, for the bias of testing for
+the exit after each step), and the tilt must matter far beyond that allowance.
 
 Planted in a copy of the oracle, the sheet-specific mistakes this pin catches
 (tilt 30 deg, A < 0, 4000 paths per energy): the sheet's radial phase dropped
@@ -60,7 +61,7 @@ def test_oracle_matches_the_cartesian_solution_with_a_tilted_sheet(orc, golden):
     flat = {c["params"]["polarity"]: np.array(c["J"]) for c in json.load(open(PDE))["cases"]
             if c["species_name"] == "proton" and c["name"] == "flat_sheet"}
     tilted = [c for c in golden["cases"] if c["kind"] == "tilted"]
-    assert len(tilted) == 3
+    assert len(tilted) == 5
     for c in tilted:
         res = orc.run(c["params"], c["species"], T0, [PATHS] * len(T0), seed=29)
         assert np.all(res["status"] == orc.EXIT)
