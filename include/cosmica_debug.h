@@ -37,6 +37,15 @@ cosmica_status cosmica_debug_curand_philox(uint32_t n, uint64_t seed, const uint
 cosmica_status cosmica_debug_normals64(uint64_t seed, uint64_t pid0, uint32_t n, uint32_t step,
                                        double *z, void *stream);
 
+/* The mixed step's FP32 normals for step `step` of particles pid0 .. pid0+n-1 (device float
+ * [3 n]), built with the mixed kernels' floating-point flags; with words != NULL also the
+ * Philox4x32-10 block each particle's normals come from (device uint32 [4 n]).  Box-Muller
+ * on that block: u = ((x >> 9) + 1/2) 2^-23 for each word x, z0 = rho0 cos(2 pi u1),
+ * z1 = rho0 sin(2 pi u1), z2 = rho2 cos(2 pi u3), rho = sqrt(-2 ln u).  INVALID also for
+ * n > 2^28. */
+cosmica_status cosmica_debug_normals32(uint64_t seed, uint64_t pid0, uint32_t n, uint32_t step,
+                                       float *z, uint32_t *words, void *stream);
+
 /* The FP64 step's deterministic elementary function `which` (0 exp, 1 log, 2 sin, 3 cos,
  * 4 tanh, 5 atan) on device arrays x, y of length n. */
 cosmica_status cosmica_debug_fn64(int32_t which, uint32_t n, const double *x, double *y, void *stream);

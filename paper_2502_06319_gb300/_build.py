@@ -3,7 +3,7 @@
 Each translation unit gets the floating-point flags its arithmetic needs:
   * k_fp64.cu, k_spectrum.cu: -fmad=false -- FP64 expressions evaluated exactly
     as written (no FMA contraction), so the FP64 path is reproducible bit for bit;
-  * k_mixed.cu, k_serve.cu: -ftz=true -prec-div=false -prec-sqrt=false
+  * k_mixed.cu, k_serve.cu, k_debug32.cu: -ftz=true -prec-div=false -prec-sqrt=false
     -fmad=false -- the mixed path deliberately uses the SFU approximations, and
     writes every FMA explicitly so that its rounding is the same in every
     kernel and inlining context;
@@ -41,6 +41,7 @@ UNITS = {
     "server.cu": [],
     "k_noalloc.cu": [],
     "k_debug_curand.cu": [],
+    "k_debug32.cu": MIXED_FLAGS,
 }
 
 

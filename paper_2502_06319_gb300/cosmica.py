@@ -165,11 +165,12 @@ def lib():
             L.cosmica_debug_philox.argtypes = [C.c_uint32, P, C.c_uint32, C.c_uint32, P, P]
             L.cosmica_debug_curand_philox.argtypes = [C.c_uint32, C.c_uint64, P, P, P, P]
             L.cosmica_debug_normals64.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, P, P]
+            L.cosmica_debug_normals32.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, P, P, P]
             L.cosmica_debug_fn64.argtypes = [C.c_int32, C.c_uint32, P, P, P]
             L.cosmica_debug_eval.argtypes = [P, C.POINTER(cosmica_species), C.c_int32, C.c_uint32, P, P, P]
             for name in ("cosmica_model_create", "cosmica_propagate", "cosmica_spectrum", "cosmica_batch_create",
                          "cosmica_batch_run", "cosmica_batch_spectrum", "cosmica_batch_spectrum_hist", "cosmica_autotune", "cosmica_debug_philox",
-                         "cosmica_debug_curand_philox", "cosmica_debug_normals64", "cosmica_debug_fn64",
+                         "cosmica_debug_curand_philox", "cosmica_debug_normals64", "cosmica_debug_normals32", "cosmica_debug_fn64",
                          "cosmica_debug_eval"):
                 getattr(L, name).restype = s
             _lib = L
@@ -497,6 +498,10 @@ def cosmica_debug_curand_philox(seed: int, subseq, offset, out, stream=None):
 
 def cosmica_debug_normals64(seed: int, pid0: int, n: int, step: int, z, stream=None):
     _check(lib().cosmica_debug_normals64(seed, pid0, n, step, _ptr(z), _stream(stream)))
+
+
+def cosmica_debug_normals32(seed: int, pid0: int, n: int, step: int, z, words=None, stream=None):
+    _check(lib().cosmica_debug_normals32(seed, pid0, n, step, _ptr(z), _ptr(words), _stream(stream)))
 
 
 FN_CODES = {"exp": 0, "log": 1, "sin": 2, "cos": 3, "tanh": 4, "atan": 5}

@@ -1223,6 +1223,15 @@ extern "C" cosmica_status cosmica_debug_normals64(uint64_t seed, uint64_t pid0, 
     return e == cudaSuccess ? COSMICA_OK : cuda_fail(e, "normals probe");
 }
 
+extern "C" cosmica_status cosmica_debug_normals32(uint64_t seed, uint64_t pid0, uint32_t n, uint32_t step,
+                                                  float *z, uint32_t *words, void *stream)
+{
+    if (n && !z) return fail(COSMICA_ERR_INVALID, "NULL array");
+    if (n > (1u << 28)) return fail(COSMICA_ERR_INVALID, "n = %u too large for one probe", n);
+    cudaError_t e = launch_debug_normals32(seed, pid0, n, step, z, words, (cudaStream_t)stream);
+    return e == cudaSuccess ? COSMICA_OK : cuda_fail(e, "FP32 normals probe");
+}
+
 extern "C" cosmica_status cosmica_debug_fn64(int32_t which, uint32_t n, const double *x, double *y, void *stream)
 {
     if (which < 0 || which > 5) return fail(COSMICA_ERR_INVALID, "function code %d", which);

@@ -119,6 +119,8 @@ cudaError_t launch_debug_eval32(const DevParams *prm, const DevSpecies *spc, uin
 cudaError_t launch_debug_fn64(int which, uint32_t n, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_debug_normals64(uint64_t seed, uint64_t pid0, uint32_t n, uint32_t step, double *z,
                                    cudaStream_t s);
+cudaError_t launch_debug_normals32(uint64_t seed, uint64_t pid0, uint32_t n, uint32_t step, float *z,
+                                   uint32_t *words, cudaStream_t s);
 cudaError_t launch_debug_philox(uint32_t n, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                                 cudaStream_t s);
 cudaError_t launch_debug_curand_philox(uint32_t n, uint64_t seed, const unsigned long long *subseq,

@@ -58,6 +58,8 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert L.cosmica_batch_spectrum_hist(None, None, 0, None, None, None, None, None, None) == cz.ERR_INVALID
     assert b"batch is NULL" in L.cosmica_last_error()
     assert L.cosmica_debug_fn64(9, 0, None, None, None) == cz.ERR_INVALID
+    assert L.cosmica_debug_normals32(1, 0, 4, 0, None, None, None) == cz.ERR_INVALID
+    assert L.cosmica_debug_normals32(1, 0, 0, 0, None, None, None) == cz.OK   # n = 0: nothing to do
 
 
 def test_invalid_model_extensions_are_rejected_on_the_host():

@@ -94,6 +94,47 @@ def test_fp64_normals_bit_identical(orc):
         assert np.array_equal(z.cpu().numpy().reshape(n, 3), orc.normals(seed, pid0, n, step))
 
 
+
+def test_fp32_normals_within_their_error_bound(orc):
+    """The mixed step's normals (FP32, SFU approximations) against Box-Muller in FP64 on the
+    same Philox words.  The words must be the oracle's block for (seed, pid, step); each word
+    maps to u = ((x >> 9) + 1/2) 2^-23, and z0 = rho0 cos(2 pi u1), z1 = rho0 sin(2 pi u1),
+    z2 = rho2 cos(2 pi u3), rho = sqrt(-2 ln u) -- the pairing of the FP64 step, so that mixed
+    and FP64 paths draw the same noise.  The bound is built from the documented maximum errors
+    of the approximations used: __logf 2^-21.41 absolute on [0.5, 2] and 3 ulp elsewhere,
+    __sincosf 2^-21.41 absolute on [-pi, pi], the approximate square root 3 ulp, the rounded
+    angle 2 pi u - pi (FP32 constants and one fma), with a factor 4 of margin."""
+    t = torch()
+    for seed, pid0, step in ((1, 0, 0), (2**63 + 5, 2**40 - 3, 4_000_000)):
+        n = 1 << 20
+        z = t.empty(3 * n, dtype=t.float32, device="cuda")
+        w = t.empty(4 * n, dtype=t.int32, device="cuda")
+        cz.cosmica_debug_normals32(seed, pid0, n, step, z, w)
+        t.cuda.synchronize()
+        z = z.cpu().numpy().reshape(n, 3).astype(np.float64)
+        w = w.cpu().numpy().view(np.uint32).reshape(n, 4)
+        pid = np.arange(pid0, pid0 + n, dtype=np.uint64)
+        ctr = np.stack([np.full(n, step, np.uint64), pid & 0xFFFFFFFF, pid >> np.uint64(32),
+                        np.zeros(n, np.uint64)], axis=1).astype(np.uint32)
+        assert np.array_equal(w, orc.philox(ctr, (seed & 0xFFFFFFFF, seed >> 32)))
+        u = ((w >> 9).astype(np.float64) + 0.5) * 2.0**-23
+        rho0, rho2 = np.sqrt(-2.0 * np.log(u[:, 0])), np.sqrt(-2.0 * np.log(u[:, 2]))
+        ref = np.stack([rho0 * np.cos(2 * np.pi * u[:, 1]), rho0 * np.sin(2 * np.pi * u[:, 1]),
+                        rho2 * np.cos(2 * np.pi * u[:, 3])], axis=1)
+        rho = np.stack([rho0, rho0, rho2], axis=1)
+        lnu = np.stack([np.log(u[:, 0])] * 2 + [np.log(u[:, 2])], axis=1)
+        e_ln = 2.0**-21.41 * np.maximum(1.0, np.abs(lnu))      # error of ln u
+        d_rho = np.minimum(np.sqrt(2.0 * e_ln), 2.0 * e_ln / rho) + 3.0 * 2.0**-23 * rho
+        d_ang = 2.0**-21.41 + 4.0e-7                             # sincos + rounded angle
+        tol = 4.0 * (d_rho + rho * d_ang + 2.0**-24 * np.abs(ref))
+        err = np.abs(z - ref)
+        assert np.all(err <= tol), (float((err / tol).max()), np.unravel_index(np.argmax(err / tol), err.shape))
+        assert abs(z.mean()) < 5.0 / np.sqrt(z.size) and abs(z.var() - 1.0) < 0.01
+        # paired with the FP64 step's normals (whose uniforms keep all 32 bits)
+        z64 = orc.normals(seed, pid0, n, step)
+        for c in range(3):
+            assert np.corrcoef(z[:, c], z64[:, c])[0, 1] > 0.99999
+
 # ------------------------------------------------------------ coefficients --
 _ORACLE_NAMES = {"V": "V", "Gam": "Gam", "Kpar": "Kpar", "Krr": "Krr", "Ktt": "Ktt", "Kpp": "Kpp",
                  "Krp": "Krp", "Ar": "Ar", "Ath": "Ath", "Aph": "Aph", "L00": "L00", "L11": "L11",
