@@ -655,7 +655,8 @@ def main():
             "scaling": "strong" if strong else "weak", "vs_baseline": None,
             "dtype": "f32+ff" if prec == cz.PREC_MIXED else ("f32+f64acc" if prec == cz.PREC_MIXED_F64ACC else "f64"),
             "data": "synthetic",
-            "config": {"workload": desc, "particles": n_total * (world if strong else 1),
+            "config": {"workload": desc,
+                       "particles": sum(i[3] for i in items_spec) if strong else n_total * world,
                        "particles_per_gpu": n_total, "spectra_per_step": n_spec_all,
                        "precision": args.precision, "formulation": args.formulation,
                        "tuning": {"block": tune.block, "blocks_per_sm": tune.blocks_per_sm,
