@@ -119,6 +119,34 @@ class Job:
         return int(sum(self.n_per_energy))
 
 
+# Particle identities of a rank's replica start at rank * PID_STRIDE (weak scaling).
+PID_STRIDE = 1 << 40
+
+
+def items_of(jobs, rank: int = 0):
+    """Work items (param_idx, species_idx, T, n, first_pid, seed) of all jobs, with
+    de-duplicated parameter sets and species.  rank > 0 gives the replica of that
+    rank (identities and seeds offset); the partition uses rank 0's list."""
+    params, pkeys, species, skeys, items = [], {}, [], {}, []
+    pid = 0
+    base = rank * PID_STRIDE
+    for j in jobs:
+        pk = tuple(sorted(j.params.items()))
+        if pk not in pkeys:
+            pkeys[pk] = len(params)
+            params.append(j.params)
+        sk = tuple(sorted(j.species.items()))
+        if sk not in skeys:
+            skeys[sk] = len(species)
+            species.append(j.species)
+        for T, n in zip(j.T_in, j.n_per_energy):
+            items.append((pkeys[pk], skeys[sk], T, n, base + pid, j.seed + 7919 * rank))
+            pid += n
+    if pid >= PID_STRIDE:
+        raise ValueError("workload exceeds the per-rank particle-identity range")
+    return params, species, items
+
+
 def logspace(lo: float, hi: float, n: int) -> List[float]:
     return [float(x) for x in np.logspace(math.log10(lo), math.log10(hi), n)]
 

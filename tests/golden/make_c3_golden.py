@@ -26,7 +26,6 @@ sys.path.insert(0, ROOT)
 
 from oracle import oracle as O  # noqa: E402
 from paper_2502_06319_gb300 import workloads as W  # noqa: E402
-from paper_2502_06319_gb300.sharding import items_of  # noqa: E402
 
 # (parameter set, species, energy index): tilt 73 deg A > 0, 64 deg A < 0, 11 deg A < 0, 8 deg A > 0
 PICK = ((11, "proton", 25), (11, "he4", 0), (11, "electron", 14),
@@ -53,7 +52,7 @@ def select(jobs, items):
 def main():
     O.build()
     jobs = W.config3()
-    params, species, items = items_of(jobs, 0)
+    params, species, items = W.items_of(jobs, 0)
     sel = select(jobs, items)
     prm_idx, sp_idx, T, pid, seed, owner = [], [], [], [], [], []
     for k, (ii, j, e) in enumerate(sel):
