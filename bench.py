@@ -91,11 +91,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "shells", "squashed"],
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "shells", "squashed", "orbit"],
                     help="c3 (default): 64 heliospheres x 3 species x 30 energies, batched; shells: 13 "
                          "monthly observations of a 15-shell time-dependent heliosphere (Sec. II.B), proton + "
                          "He-4, batched like config 3; squashed: config 3 with the nose-squashed shock and outer "
-                         "boundary (Sec. II.B); c4: the serving bench alone")
+                         "boundary (Sec. II.B); c4: the serving bench alone; orbit: config 2's heliosphere seen from a "
+                         "detection point moving along a synthetic polar orbit (cosmica_propagate_orbit, Sec. IV.A)")
     ap.add_argument("--scaling", default="strong", choices=["strong", "weak"],
                     help="N > 1: partition one workload (strong) or give every rank a copy (weak)")
     ap.add_argument("--c4-requests", type=int, default=24, help="requests per serving run (--workload c4)")
@@ -376,6 +377,101 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def orbit_bench(args, cz, torch, prec, local):
+    """The moving detection point (Sec. IV.A): config 2's heliosphere and energies, each energy's
+    sample split among the positions of a synthetic polar orbit, through cosmica_propagate_orbit and
+    cosmica_spectrum; W warm-up and K timed passes (CUDA events, L2 flushed before each), then passes
+    timed end to end on the host."""
+    n = max(1, int(round(20000 * args.scale)))
+    job = W.config2(n)
+    orbit = W.polar_orbit()
+    model = cz.Model(cz.make_params(job.params, prec))
+    sp = cz.make_species(job.species)
+    bins = cz.make_bins(job.bins.P_min, job.bins.P_max, job.bins.n)
+    nE, nb = len(job.T_in), job.bins.n
+    out = cz.ExitBuffers(job.n_particles)
+    J = torch.empty(nE, dtype=torch.float64, device="cuda")
+    S = torch.empty_like(J)
+    H = torch.empty(nE * (nb + 3), dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+
+    def one_pass(events=None):
+        if events:
+            events[0].record(stream)
+        cz.cosmica_propagate_orbit(model.h, sp, job.T_in, job.n_per_energy, orbit, job.seed, out, stream=stream)
+        if events:
+            events[1].record(stream)
+        cz.cosmica_spectrum(out, sp, job.T_in, bins, J, S, H, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_pass()
+    stream.synchronize()
+    steps_pass = int(out.steps.to(torch.int64).sum().item())      # the same every pass (fixed identities)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = cz.cosmica_launch_count()
+    ms, kern = [], []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[2].record(stream)
+            one_pass(ev[:2])
+            ev[3].record(stream)
+        ev[3].synchronize()
+        ms.append(ev[2].elapsed_time(ev[3]))
+        kern.append(ev[0].elapsed_time(ev[1]))
+    launches = cz.cosmica_launch_count() - launches0
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    J_h = torch.empty(nE, dtype=torch.float64, pin_memory=True)
+    S_h = torch.empty(nE, dtype=torch.float64, pin_memory=True)
+    H_h = torch.empty(nE * (nb + 3), dtype=torch.int64, pin_memory=True)
+    e2e_s = 0.0
+    n_e2e = max(1, args.e2e_steps)
+    for _ in range(n_e2e):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            one_pass()
+            J_h.copy_(J, non_blocking=True)
+            S_h.copy_(S, non_blocking=True)
+            H_h.copy_(H, non_blocking=True)
+        stream.synchronize()
+        e2e_s += time.perf_counter() - t0
+    model.close()
+    nI = nE * len(orbit)                     # one work item per (position, energy)
+    tot_ms, k_ms = sum(ms), sum(kern) / len(kern)
+    steps_per_s = steps_pass * args.steps / (tot_ms * 1e-3)
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    f_mhz = clk.get("sm_mhz") or 2070.0
+    peak = SM_LANES_PER_CLK * sm_count * f_mhz * 1e6 / 1e12
+    alg_total = sum(ALG_INST_PER_STEP.values())
+    achieved = alg_total * steps_pass / (k_ms * 1e-3) / 1e12
+    r_lo, r_hi = min(q[0] for q in orbit), max(q[0] for q in orbit)
+    return {"metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64acc" if prec == cz.PREC_MIXED_F64ACC else ("f64" if prec == cz.PREC_FP64 else "f32+ff"),
+            "data": "synthetic",
+            "config": {"workload": f"orbit: config2's heliosphere (full model), proton, {nE} energies x {n} "
+                                   f"quasi-particles, each energy's sample split over {len(orbit)} equal-time "
+                                   f"positions of a synthetic polar orbit ({r_lo:.2f}-{r_hi:.2f} AU, inclination "
+                                   f"80 deg)", "particles": job.n_particles, "precision": args.precision,
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "spectra_per_s": args.steps / (tot_ms * 1e-3),
+            "e2e": {"value": steps_pass * n_e2e / e2e_s, "unit": "steps/s",
+                    "h2d_bytes_per_step": nI * 64 + 2 * (nI + 1) * 8 + nI * 4,
+                    "d2h_bytes_per_step": 2 * nE * 8 + nE * (nb + 3) * 8, "passes": n_e2e},
+            "gpu_launches": launches, "clocks": clk,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
+                         "frac": achieved / peak, "traffic": None, "alg_inst_total": alg_total,
+                         "kernel_ms_per_launch": k_ms, "algorithmic_bytes_per_step": 0.0}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -418,6 +514,13 @@ def main():
                 "gpu_launches": cz.cosmica_launch_count() - launches0, "clocks": clk}
         if rank == 0:
             print(json.dumps(line), flush=True)
+        return
+
+    if args.workload == "orbit":
+        if world > 1:
+            raise SystemExit("--workload orbit runs on one GPU")
+        line = orbit_bench(args, cz, torch, prec, local)
+        print(json.dumps(line), flush=True)
         return
 
     jobs, desc = workload(args)

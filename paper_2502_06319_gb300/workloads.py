@@ -16,7 +16,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
-from typing import Dict, List
+from typing import Dict, List, Tuple
 
 import numpy as np
 
@@ -170,6 +170,27 @@ def config2(n_per: int = 20_000, n_e: int = 30) -> Job:
     j = config1(n_per, n_e)
     j.name, j.mixed = "c2", True
     return j
+
+
+def polar_orbit(n_pos: int = 12, a_AU: float = 3.35, e: float = 0.6,
+                incl_deg: float = 80.0) -> List[Tuple[float, float, float, float]]:
+    """A synthetic out-of-ecliptic orbit for the moving detection point (Sec. IV.A): a Kepler
+    ellipse of semi-major axis a_AU and eccentricity e (perihelion 1.34 AU, aphelion 5.36 AU by
+    default) inclined incl_deg to the ecliptic, with its perihelion on the line of nodes, so
+    that the latitude sweeps fastest near the Sun.  Sampled at n_pos equal steps of mean
+    anomaly, i.e. of time: (r [AU], theta [rad], phi [rad], weight 1) per position."""
+    out = []
+    inc = math.radians(incl_deg)
+    for k in range(n_pos):
+        M = 2.0 * math.pi * (k + 0.5) / n_pos
+        E = M + e * math.sin(M)
+        for _ in range(60):                       # Kepler's equation E - e sin E = M
+            E -= (E - e * math.sin(E) - M) / (1.0 - e * math.cos(E))
+        r = a_AU * (1.0 - e * math.cos(E))
+        nu = 2.0 * math.atan2(math.sqrt(1.0 + e) * math.sin(E / 2.0), math.sqrt(1.0 - e) * math.cos(E / 2.0))
+        x, y, z = r * math.cos(nu), r * math.sin(nu) * math.cos(inc), r * math.sin(nu) * math.sin(inc)
+        out.append((r, math.acos(z / r), math.atan2(y, x) % (2.0 * math.pi), 1.0))
+    return out
 
 
 def config3_param_sets(seed: int = 20250210, n_sets: int = 64) -> List[Dict[str, float]]:
