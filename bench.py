@@ -158,6 +158,9 @@ def probe_latency(cz, torch):
 
 def workload(args):
     """Jobs (one per spectrum) of the chosen configuration."""
+    if args.workload == "orbit":
+        raise SystemExit("--workload orbit is timed by our arm only (orbit_bench); the reference arm "
+                         "times the batched workloads")
     if args.workload == "c4":
         return [r.job for r in W.config4(n_requests=args.c4_requests)], "config4 request sample"
     if args.workload == "c1":

@@ -6,7 +6,9 @@ every energy is divided among the positions of the detector's orbit.
     not depend on the start angles at all (bit for bit), and the
     orbit-averaged spectrum equals the weighted mean of the steady transport
     equation's solutions at the orbit's radii (independent Crank-Nicolson
-    solver), up to the Euler-Maruyama step bias.
+    solver), up to the Euler-Maruyama step bias;
+  * the synthetic polar orbit the orbit bench uses samples equal times
+    (Kepler's equation recovered from the radii).
 """
 import math
 
@@ -78,3 +80,25 @@ def test_orbit_spectrum_is_weighted_mean_of_pde_solutions(orc):
     # a swapped split (3/4 at 10 AU) is excluded
     swapped = 0.25 * J1 + 0.75 * J10
     assert np.all(np.abs(J - swapped) > 3.0 * S)
+
+
+def test_synthetic_polar_orbit_samples_equal_times():
+    # the orbit of `bench.py --workload orbit`: a Kepler ellipse sampled at equal steps of mean
+    # anomaly.  From each radius alone, cos E = (1 - r/a)/e gives the eccentric anomaly (up to
+    # the half of the orbit) and M = E - e sin E must fall on (k + 1/2) 2 pi / n
+    a, e, inc, n = 3.35, 0.6, 80.0, 12
+    orbit = W.polar_orbit(n, a, e, inc)
+    assert len(orbit) == n and all(q[3] == 1.0 for q in orbit)
+    p = W.params()
+    for k, (r, th, ph, _) in enumerate(orbit):
+        assert a * (1 - e) < r < a * (1 + e) and p["r_in"] < r < p["R_out"]
+        assert math.radians(90.0 - inc) - 1e-12 <= th <= math.radians(90.0 + inc) + 1e-12
+        assert 0.0 <= ph < 2.0 * math.pi
+        E = math.acos((1.0 - r / a) / e)
+        M = E - e * math.sin(E)
+        Mk = 2.0 * math.pi * (k + 0.5) / n
+        assert min(abs(M - Mk), abs(2.0 * math.pi - M - Mk)) < 1e-9, (k, M, Mk)
+    # the perihelion passage sweeps the latitude fastest: both ends of the sampled orbit
+    # (next to perihelion) are at high latitude, the middle (aphelion) near the ecliptic
+    lat = [90.0 - math.degrees(q[1]) for q in orbit]
+    assert lat[0] > 45.0 and lat[-1] < -45.0 and abs(lat[n // 2]) < 10.0
