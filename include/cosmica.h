@@ -379,7 +379,11 @@ typedef struct {
 
 /* Launch shape and scheduling of the persistent kernel.  Passing NULL selects
  * block 128, the most resident blocks, compaction every 64 steps, no graph,
- * most-expensive-first queue order. */
+ * most-expensive-first queue order -- except that a launch with fewer than 8
+ * particles per resident lane (bound by its slowest paths, which step faster
+ * when fewer warps share an SM) takes 4 blocks of 128 per SM.  The same
+ * default shapes the launches of cosmica_propagate and
+ * cosmica_propagate_orbit. */
 typedef struct {
     uint32_t block;           /* threads per block (32..256; 0 = 128)                   */
     uint32_t blocks_per_sm;   /* resident blocks per SM requested (0 = as many as fit)  */

@@ -363,6 +363,13 @@ PersistentShape shape_for(MixedVariant v, const cosmica_tuning *t, uint64_t n_to
     int max_b = mixed_max_blocks_per_sm(v, block, period != 0);
     if (max_b < 1) max_b = 1;
     int bps = (t && t->blocks_per_sm) ? (int)t->blocks_per_sm : max_b;
+    if (!t) {
+        // no tuning given: a launch with few particles per resident lane is bound by its slowest
+        // paths, which step faster when fewer warps share an SM (the autotuner picks 16 warps per
+        // SM for 6e5 particles, about 5 per lane, and every resident block from 1.5e6 up)
+        const uint64_t lanes = (uint64_t)num_sms() * (uint64_t)max_b * block;
+        if (n_total < 8ull * lanes) bps = std::max(1, (int)(512u / block));
+    }
     bps = std::min(bps, max_b);
     uint64_t grid = (uint64_t)num_sms() * (uint64_t)bps;
     const uint64_t need = (n_total + block - 1) / block;   // never more blocks than particles
