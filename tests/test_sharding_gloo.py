@@ -132,3 +132,22 @@ def test_single_rank_passthrough():
     merge_histograms(None, torch.zeros(3))
     with pytest.raises(ValueError):
         items_of([W.Job(W.params(), W.PROTON, [1.0], [PID_STRIDE], seed=1)], 0)
+
+
+def test_pieces_carry_their_global_rows_into_the_work_items():
+    # what bench.py hands to cosmica_batch_run on each rank: the pieces' work items carry
+    # exit_item_plus1 = global row + 1 (the histogram row of the whole item list), their own
+    # particle count and first identity; an unsharded list carries 0 (its own numbering)
+    from paper_2502_06319_gb300 import cosmica as cz
+    _, _, items = items_of(_small_workload(), 0)
+    for world in (2, 3):
+        for rank in range(world):
+            share = partition(items, world, rank)
+            arr = cz.make_items([p for _, p in share], [g for g, _ in share])
+            for k, (g, p) in enumerate(share):
+                w = arr[k]
+                assert w.exit_item_plus1 == g + 1 and w.n == p[3] and w.first_pid == p[4]
+                assert (w.param_idx, w.species_idx, w.T_GeVn, w.seed) == (items[g][0], items[g][1],
+                                                                           items[g][2], items[g][5])
+    arr = cz.make_items(items)
+    assert all(arr[k].exit_item_plus1 == 0 for k in range(len(items)))
