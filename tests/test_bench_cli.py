@@ -1,7 +1,8 @@
 """bench.py's command-line contract on the CPU: the reference arm (the FP64
 oracle on the host cores) prints one JSON line with the keys the contract
-names, only rank 0 prints, and our arm refuses to run without a CUDA GPU
-instead of falling back to the CPU."""
+names, only rank 0 prints, our arm refuses to run without a CUDA GPU instead
+of falling back to the CPU, and the clock record of the timed region reports
+the median SM clock and every throttle reason that was active."""
 import json
 import os
 import subprocess
@@ -47,3 +48,31 @@ def test_our_arm_fails_loudly_without_a_gpu():
     r = _bench("--steps", "1", "--warmup", "0")
     assert r.returncode != 0
     assert "CUDA GPU" in (r.stdout + r.stderr)
+
+
+def test_clock_record_from_a_fake_nvidia_smi():
+    # the clock and throttle record of the timed region, parsed from nvidia-smi's CSV rows
+    # (index, sm, max sm, power, active mask, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap);
+    # no GPU and no nvidia-smi: the sampler's process is a stand-in that has already ended
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Ended:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c = bench.Clocks(0)
+    c.f.write("0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+              "0, 2055, 2070, 1380.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+              "0, 2070, 2070, 1390.2, 0x4, Not Active, Not Active, Not Active, Active\n"
+              "garbage line\n")
+    c.proc = Ended()
+    rec = c.stop()
+    assert rec == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c = bench.Clocks(0)
+    c.f.write("0, 1200, 2070, 700.0, 0x8, Active, Not Active, Active, Not Active\n")
+    c.proc = Ended()
+    assert c.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
