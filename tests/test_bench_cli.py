@@ -76,3 +76,16 @@ def test_clock_record_from_a_fake_nvidia_smi():
     c.f.write("0, 1200, 2070, 700.0, 0x8, Active, Not Active, Active, Not Active\n")
     c.proc = Ended()
     assert c.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_stratified_samples_span_the_whole_item_list():
+    # the samples the plain FP64 path and the oracle baseline are timed on: the first m particles
+    # of every non-empty item (capped at its count), or the first particle of every k-th item
+    sys.path.insert(0, ROOT)
+    import bench
+    items = [(0, 0, 0.1 * (i + 1), n, 1000 * i, 7) for i, n in enumerate([5, 0, 1, 9, 3, 2, 8, 4])]
+    smp, how = bench.stratified(items, 24)            # 24 // 8 = 3 per item
+    assert [s[3] for s in smp] == [3, 1, 3, 3, 2, 3, 3] and "first 3" in how
+    assert [s[4] for s in smp] == [0, 2000, 3000, 4000, 5000, 6000, 7000]   # identities kept
+    smp, how = bench.stratified(items, 3)             # every 2nd item, one particle each
+    assert [(s[4], s[3]) for s in smp] == [(0, 1), (2000, 1), (4000, 1), (6000, 1)] and "every 2-th" in how
