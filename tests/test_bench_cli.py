@@ -89,3 +89,26 @@ def test_stratified_samples_span_the_whole_item_list():
     assert [s[4] for s in smp] == [0, 2000, 3000, 4000, 5000, 6000, 7000]   # identities kept
     smp, how = bench.stratified(items, 3)             # every 2nd item, one particle each
     assert [(s[4], s[3]) for s in smp] == [(0, 1), (2000, 1), (4000, 1), (6000, 1)] and "every 2-th" in how
+
+
+def test_spectrum_error_maps_the_stored_items_onto_the_full_workload():
+    # the twelve stored oracle items of config 3 must be found in today's config-3 item list by
+    # (first particle identity, count) -- the input generator and the stored values agree -- and
+    # the error record flags a deviation beyond 0.5 %
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2502_06319_gb300 import workloads as W
+    _, _, items = W.items_of(W.config3(), 0)
+    g = json.load(open(bench.GOLDEN_C3))
+    J = [float("nan")] * len(items)
+    S = [0.0] * len(items)
+    key = {(it[4], it[3]): k for k, it in enumerate(items)}
+    for rec in g["items"]:
+        k = key[(rec["first_pid"], rec["n"])]
+        assert abs(items[k][2] - rec["T"]) < 1e-12
+        J[k], S[k] = rec["J"], rec["sigma"]
+    e = bench.spectrum_error(items, J, S)
+    assert e["items"] == 12 and e["max_abs_rel"] == 0.0 and e["within_0.5pct_and_3sigma"]
+    k = key[(g["items"][0]["first_pid"], g["items"][0]["n"])]
+    J[k] *= 1.006
+    assert not bench.spectrum_error(items, J, S)["within_0.5pct_and_3sigma"]
